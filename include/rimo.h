@@ -1,0 +1,232 @@
+/*
+ * rimo.h - C ABI of the GB300 widefield radio-interferometric measurement operator.
+ *
+ * The library applies the widefield measurement operator Phi, its adjoint Phi^dagger
+ * and the composite Phi^dagger Phi in hybrid w-stacking / w-projection form
+ * (Dabbech & Wiaux, Section 3, Eq. 6 - Eq. 8) on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are rimo_cfloat (two float32, real first): the memory layout of
+ * numpy complex64 / torch.complex64.
+ *
+ * Images are row-major [ny][nx].  Pixel (i, j) sits at direction cosines
+ * l = (j - nx/2) * fov_x / nx and m = (i - ny/2) * fov_y / ny.
+ *
+ * Visibility vectors are in the caller's order: entry k belongs to row k of the uvw
+ * array given to rimo_plan_create.  uvw is in wavelengths.
+ *
+ * Ownership: the caller owns every input and output buffer ("_dev" pointers are
+ * device memory the caller allocated, e.g. torch tensors).  A plan owns all the
+ * device memory it allocates (de-gridding matrix, holographic blocks, scratch grids)
+ * and frees it in rimo_plan_destroy.
+ *
+ * Streams: work is enqueued on the caller's stream without host synchronisation,
+ * except where an entry point says it synchronises.  A plan holds scratch grids,
+ * so two applies of one plan must not run concurrently on different streams.
+ * Distinct plans are independent.
+ *
+ * Errors: every call returns a rimo_status; on failure rimo_last_error() gives a
+ * thread-local message.  No C++ exception crosses this interface.  Asynchronous
+ * CUDA errors of enqueued work surface at a later call that synchronises.
+ */
+#ifndef RIMO_H
+#define RIMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rimo_cfloat { float re, im; } rimo_cfloat;
+
+typedef enum rimo_status {
+    RIMO_OK = 0,
+    RIMO_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range        */
+    RIMO_ERR_OOM = 2,         /* a device or host allocation failed                   */
+    RIMO_ERR_BUDGET = 3,      /* the requested mode does not fit mem_budget_bytes     */
+    RIMO_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed          */
+    RIMO_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out                   */
+    RIMO_ERR_UNSUPPORTED = 6, /* the plan's mode or sizes do not support this call    */
+    RIMO_ERR_STATE = 7        /* the call needs a step that has not been done yet     */
+} rimo_status;
+
+typedef enum rimo_mode {
+    RIMO_MODE_AUTO = 0,        /* decision tree of Section 3.4 / Fig. 2              */
+    RIMO_MODE_STORED_G = 1,    /* precompute and store the de-gridding matrix G      */
+    RIMO_MODE_HOLOGRAPHIC = 2, /* precompute H_p = G_p^dagger G_p (Section 3.3)      */
+    RIMO_MODE_SURROGATE = 3,   /* kernels generated on the fly by the learned MLP    */
+    RIMO_MODE_ONTHEFLY = 4     /* exact kernels generated on the fly                 */
+} rimo_mode;
+
+typedef enum rimo_n_weight {
+    RIMO_NWEIGHT_NONE = 0,  /* C = exp(-2 pi i w (n - 1))              (default)      */
+    RIMO_NWEIGHT_DIV_N = 1  /* C = exp(-2 pi i w (n - 1)) / n, the 1/n of Eq. 2       */
+} rimo_n_weight;
+
+/*
+ * Plan parameters (Section 3.1 and Section 3.4).  Zero selects the default where
+ * one is named.
+ *   nx, ny            image size; powers of two in [64, 4096].
+ *   fov_x, fov_y      full field of view (radians); (fov/2)^2 * 2 * 4 < 1.
+ *   oversampling      must be 2 (the paper's o = 2).
+ *   kb_support        Kaiser-Bessel taps J per axis: odd, 3..11 (default 7).
+ *   kb_beta           KB shape (0 -> 2.34 J, the Fessler-Sutton choice for o = 2).
+ *   max_wsupport      cap on the residual w-kernel support S_w: odd, 1..9 (default 9).
+ *                     The per-visibility tile is S x S with S = S_w + J - 1 <= 19.
+ *   w_norm_frac       fraction of the w-kernel l2 norm kept by hard-thresholding
+ *                     (Section 3.1); in (0, 1], default 0.9999.
+ *   mem_budget_bytes  device memory budget m* for the stored matrices (0 = no limit).
+ *   n_wbins           number P of w-bins (0 = chosen by the cost model, Eq. 10).
+ *   n_blocks          Fourier blocks per plan (0 = by block_bytes_max).
+ *   mode              rimo_mode.
+ *   n_weight          rimo_n_weight.
+ *   plan_fraction     fraction of the data used for planning (default 0.01).
+ *   seed              seed of the planning subset.
+ *   taper_literal     0: taper the chirp's deviation from 1 (default); 1: taper C.
+ *   wkernel_L         w-kernel sampling grid per axis (0 = max(32, 2^ceil(log2(4 S_w,max)))).
+ *   tile_size         uv-tile edge in grid cells for sorting/gridding (0 = 64; 32 or 64).
+ *   block_bytes_max   upper bound of one Fourier block of G (0 = 8 GiB).
+ */
+typedef struct rimo_plan_params {
+    int32_t nx, ny;
+    double fov_x, fov_y;
+    int32_t oversampling;
+    int32_t kb_support;
+    double kb_beta;
+    int32_t max_wsupport;
+    double w_norm_frac;
+    int64_t mem_budget_bytes;
+    int32_t n_wbins;
+    int32_t n_blocks;
+    int32_t mode;
+    int32_t n_weight;
+    double plan_fraction;
+    uint64_t seed;
+    int32_t taper_literal;
+    int32_t wkernel_L;
+    int32_t tile_size;
+    int64_t block_bytes_max;
+} rimo_plan_params;
+
+/* Results of planning (stage 1 of Fig. 3) and the state of a plan. */
+typedef struct rimo_plan_info {
+    int64_t M;                 /* visibilities                                     */
+    int32_t P;                 /* w-bins                                           */
+    int32_t mode;              /* rimo_mode actually used                          */
+    int32_t p_star;            /* minimiser of the cost model over the candidates  */
+    int32_t wkernel_L;
+    int32_t max_tile;          /* largest S in the plan                            */
+    int32_t n_blocks;          /* Fourier blocks of G                              */
+    int32_t n_tiles;           /* active uv-tiles over all bins                    */
+    int64_t subset;            /* visibilities used for planning                   */
+    int64_t K;                 /* non-zeros of G: sum_k S_k^2                      */
+    int64_t g_bytes;           /* device bytes of stored G (taps + metadata)       */
+    int64_t h_bytes;           /* device bytes of stored H (0 unless built)        */
+    int64_t scratch_bytes;     /* device bytes of scratch grids                    */
+    double est_m_g;            /* Eq. 9 analogue at the chosen P, from the subset  */
+    double est_cost;           /* Eq. 10 at the chosen P                           */
+    double wr_max;             /* max |w - w_stack[bin]|                           */
+    double wsclean_p;          /* Eq. 5 bound                                      */
+    int32_t support_table[64]; /* S_w per uniform |w_r| bin                        */
+} rimo_plan_info;
+
+typedef struct rimo_plan* rimo_plan_t;
+
+/*
+ * Default parameters for an nx x ny image over fov_x x fov_y radians.
+ * Never fails; writes *p.
+ */
+void rimo_plan_params_default(rimo_plan_params* p, int32_t nx, int32_t ny, double fov_x,
+                              double fov_y);
+
+/*
+ * Plan on the host only (Section 3.4, stage 1 of Fig. 3): choose P and the mode from
+ * the planning subset without touching a GPU.  uvw: host, M x 3 row-major float64
+ * (wavelengths).  Fills *info (per-visibility fields are not computed).
+ * Errors: INVALID_ARG.
+ */
+rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_params* p,
+                               rimo_plan_info* info);
+
+/*
+ * Create a plan (stages 1 - 3 of Fig. 3): w-bins by k-means (Section 3.1), P and mode
+ * (Section 3.4), per-visibility grid coordinates, uv-tile sort and Fourier blocks
+ * (Section 3.2), and - in stored-G mode - the de-gridding matrix G on the device.
+ * uvw: host, M x 3 row-major float64 (wavelengths); copied, not retained.
+ * The plan is built on `stream`; the call synchronises the stream before returning.
+ * Errors: INVALID_ARG, OOM, BUDGET (explicit mode beyond the budget), CUDA.
+ */
+rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_params* p,
+                             void* stream, rimo_plan_t* out);
+
+/* Free a plan and all device memory it owns.  NULL is accepted. */
+rimo_status rimo_plan_destroy(rimo_plan_t plan);
+
+/* Copy the plan summary into *info (host). */
+rimo_status rimo_plan_info_get(rimo_plan_t plan, rimo_plan_info* info);
+
+/*
+ * Copy plan data to host buffers (any may be NULL): w_stack[P] (ascending w-bin
+ * values), bins[M] (w-bin of each visibility, caller order), s_w[M] (residual
+ * w-kernel support of each visibility, caller order).
+ */
+rimo_status rimo_plan_get_bins(rimo_plan_t plan, double* w_stack, int32_t* bins, int32_t* s_w);
+
+/*
+ * Copy the de-gridding taps of selected visibilities to the host (Section 3.2, G_p rows).
+ * idx[n]: caller-order visibility indices (host).  For visibility idx[q] writes
+ * g0[q], h0[q] (first grid cell along u and v, already reduced modulo the grid),
+ * S[q] (tile side) and taps[q * 19 * 19 ...]: the S x S tile, row a along u, column b
+ * along v, at taps + q * 361 (row stride S).  Synchronises `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED (plan without stored G).
+ */
+rimo_status rimo_plan_get_tiles(rimo_plan_t plan, const int64_t* idx, int64_t n, int32_t* g0,
+                                int32_t* h0, int32_t* S, rimo_cfloat* taps, void* stream);
+
+/*
+ * y = Phi x (Eq. 6).  x_dev: device, ny x nx image; y_dev: device, M visibilities in
+ * caller order.  Errors: INVALID_ARG, UNSUPPORTED (holographic-only plan), CUDA.
+ */
+rimo_status rimo_apply_phi(rimo_plan_t plan, const rimo_cfloat* x_dev, rimo_cfloat* y_dev,
+                           void* stream);
+
+/*
+ * x = Phi^dagger y = sum_p Z_p^dagger F^dagger G_p^dagger y_p (adjoint of Eq. 6).
+ * y_dev: device, M visibilities (caller order); x_dev: device, ny x nx image (overwritten).
+ */
+rimo_status rimo_apply_phi_adj(rimo_plan_t plan, const rimo_cfloat* y_dev, rimo_cfloat* x_dev,
+                               void* stream);
+
+/*
+ * out = Phi^dagger Phi x = sum_p Z_p^dagger F^dagger G_p^dagger G_p F Z_p x (Eq. 7 and Eq. 8),
+ * or with H_p in place of G_p^dagger G_p once rimo_build_holographic has run.
+ * x_dev, out_dev: device ny x nx images (distinct buffers); real_part_only != 0 writes
+ * Re{.} with zero imaginary parts (the Re{} of Eq. 4).
+ */
+rimo_status rimo_apply_phi_adj_phi(rimo_plan_t plan, const rimo_cfloat* x_dev,
+                                   rimo_cfloat* out_dev, int32_t real_part_only, void* stream);
+
+/*
+ * Build the holographic matrices H_p = G_p^dagger G_p on the device (Section 3.3) and
+ * switch rimo_apply_phi_adj_phi to them.  Needs a plan with stored G.
+ * Synchronises `stream`.  Errors: UNSUPPORTED, OOM, BUDGET, CUDA.
+ */
+rimo_status rimo_build_holographic(rimo_plan_t plan, void* stream);
+
+/* PSF: out = Phi^dagger Phi delta, delta at pixel (ny/2, nx/2); unnormalised. */
+rimo_status rimo_psf(rimo_plan_t plan, rimo_cfloat* out_dev, void* stream);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* rimo_last_error(void);
+
+/* Library version string. */
+const char* rimo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIMO_H */

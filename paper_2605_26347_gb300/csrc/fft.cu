@@ -1,0 +1,462 @@
+// The oversampled 2-D DFT F of Eq. 6 and its adjoint, as four row passes.
+//
+// Forward, for w-bin p (F Z_p of Eq. 6):
+//   rows pass  : image row i (n_x pixels) -> z = x * Z_p (grid correction and the w-layer
+//                chirp, Section 3.2) -> zero-padded 2n_x-point DFT along l, written
+//                transposed as A^T[u][i]  (2 n_x rows of n_y).
+//   cols pass  : row u of A^T -> zero-padded 2n_y-point DFT along m -> X[u][v].
+// Adjoint (Z_p^dagger F^dagger of Eq. 8):
+//   cols pass  : row u of Xh (2 n_y cells) -> 2n_y-point inverse DFT cropped to the n_y
+//                image rows -> B[i][u], transposed.
+//   rows pass  : row i of B (2 n_x cells) -> cropped inverse DFT along u -> * conj(Z_p),
+//                accumulated into the output image.
+//
+// Zero padding and cropping are exploited exactly: a 2N-point DFT of N centred samples
+// is two N-point DFTs (even and odd outputs, the odd one of pre-twiddled input), and a
+// 2N-point inverse DFT kept on N centred outputs is two N-point inverse DFTs of folded
+// inputs (even and odd outputs).  Each N-point DFT is a Stockham radix-16 FFT held in
+// registers (16 points per thread, N/16 threads), exchanging through shared memory.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace rimo {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    float2 a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = mul_mi<INV>(csub(x1, x3));
+    x0 = cadd(a0, a2);
+    x2 = csub(a0, a2);
+    x1 = cadd(a1, a3);
+    x3 = csub(a1, a3);
+}
+
+#define RS2 0.70710678118654752440f
+#define C16 0.92387953251128675613f
+#define S16 0.38268343236508977173f
+
+// W_N^k for the small radices: forward e^{-2 pi i k / N}, inverse its conjugate
+template <bool INV>
+__device__ __forceinline__ float2 w8(int k) {
+    const float c[4] = {1.f, RS2, 0.f, -RS2};
+    const float s[4] = {0.f, RS2, 1.f, RS2};
+    return make_float2(c[k], INV ? s[k] : -s[k]);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    float2 o1 = cmul(v[3], w8<INV>(1)), o2 = cmul(v[5], w8<INV>(2)), o3 = cmul(v[7], w8<INV>(3));
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 w16(int k) {  // k in [0, 9]
+    const float c[10] = {1.f, C16, RS2, S16, 0.f, -S16, -RS2, -C16, -1.f, -C16};
+    const float s[10] = {0.f, S16, RS2, C16, 1.f, C16, RS2, S16, 0.f, -S16};
+    return make_float2(c[k], INV ? s[k] : -s[k]);
+}
+
+// 16-point DFT as 4 x 4: inner DFT_4 over n1 (stride 4), twiddle W16^{n2 k1}, outer DFT_4.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    // now v[n2 + 4 k1] = A[n2][k1]
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) v[n2 + 4 * k1] = cmul(v[n2 + 4 * k1], w16<INV>(n2 * k1));
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a = v[0 + 4 * k1], b = v[1 + 4 * k1], c = v[2 + 4 * k1], d = v[3 + 4 * k1];
+        dft4<INV>(a, b, c, d);
+        t[k1 + 0] = a;
+        t[k1 + 4] = b;
+        t[k1 + 8] = c;
+        t[k1 + 12] = d;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2* v) {
+    if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<INV>(v);
+    else dft16<INV>(v);
+}
+
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// One Stockham stage of radix R after NS points have been combined (NS * R <= N).
+// Thread t owns butterflies j = t + q T (q < 16/R, T = N/16); butterfly j reads
+// a[j + r N/R] and writes a'[(j / NS) NS R + j % NS + r NS].
+template <int N, int R, int NS, bool INV, bool FIRST, bool LAST>
+__device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tw2N) {
+    constexpr int T = N / 16;
+    constexpr int Q = 16 / R;
+    if (!FIRST) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q * R + r] = sm[pidx(t + q * T + r * (N / R))];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (NS > 1) {
+            const int jm = (t + q * T) & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const int e = r * jm * (N / (NS * R));
+                float2 w = __ldg(&tw2N[2 * e]);
+                v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+            }
+        }
+        dft_r<R, INV>(&v[q * R]);
+    }
+    if (!LAST) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = t + q * T;
+            const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[pidx(base + r * NS)] = v[q * R + r];
+        }
+        __syncthreads();
+    }
+}
+
+// Radix plan: 16, 16, ..., then the remainder (2, 4, 8 or 16).
+template <int N>
+struct Plan16 {
+    static constexpr int R_LAST = (N == 64) ? 4 : (N == 128) ? 8 : (N == 256) ? 16
+                                : (N == 512) ? 2 : (N == 1024) ? 4 : (N == 2048) ? 8 : 16;
+};
+
+// In: v[m] = element t + T m of the input.  Out: element t + T m of the output is
+// v[out_slot<N>(m)].  All threads of the block must call it (block-wide barriers).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_n(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tw2N) {
+    constexpr int RL = Plan16<N>::R_LAST;
+    if constexpr (N == 64 || N == 128 || N == 256) {
+        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tw2N);
+        fft_stage<N, RL, 16, INV, false, true>(v, sm, t, tw2N);
+    } else {
+        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tw2N);
+        fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tw2N);
+        fft_stage<N, RL, 256, INV, false, true>(v, sm, t, tw2N);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ int out_slot(int m) {
+    constexpr int RL = Plan16<N>::R_LAST;
+    constexpr int Q = 16 / RL;
+    return (m % Q) * RL + m / Q;
+}
+
+// e^{-2 pi i w dn} from the double-float phase w * dn, reduced modulo 1 before sincos.
+// The product and reduction keep ~48 significant bits (error-free FMA product), which is
+// the FP64-accurate w-phase argument; only the final sincospi is single precision.
+__device__ __forceinline__ float2 wphase(float w_hi, float w_lo, float2 d) {
+    float p = w_hi * d.x;
+    float e = fmaf(w_hi, d.x, -p);
+    e = fmaf(w_hi, d.y, e);
+    e = fmaf(w_lo, d.x, e);
+    float k = rintf(p);
+    float r = (p - k) + e;
+    float s, c;
+    sincospif(2.0f * r, &s, &c);
+    return make_float2(c, -s);
+}
+
+struct ZArgs {
+    const float2* dn;   // quarter table [|i_c|][|j_c|]
+    int dn_ld;
+    const float* gcx;
+    const float* gcy;
+    float w_hi, w_lo;
+    int div_n;
+};
+
+// Z_p(i, j) = gc_x[j] gc_y[i] e^{-2 pi i w dn(l_j, m_i)} [/ (1 + dn)]
+__device__ __forceinline__ float2 z_factor(const ZArgs& z, int i, int j, int ic, int jc) {
+    float2 d = __ldg(&z.dn[abs(ic) * z.dn_ld + abs(jc)]);
+    float2 ph = wphase(z.w_hi, z.w_lo, d);
+    float g = __ldg(&z.gcx[j]) * __ldg(&z.gcy[i]);
+    if (z.div_n) g = g / (1.0f + (d.x + d.y));
+    return make_float2(ph.x * g, ph.y * g);
+}
+
+// ----------------------------------------------------------------------------- forward rows
+// grid: ny / RB blocks of RB * N/16 threads; block b transforms image rows [b RB, b RB + RB).
+template <int N, int RB>
+__global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At,
+                                                                int ny, ZArgs z, const float2* __restrict__ tw2N) {
+    constexpr int T = N / 16;
+    extern __shared__ float2 smem[];
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    float2* sm = smem + g * (N + N / 16);
+    const int i = blockIdx.x * RB + g;
+    const int ic = i - ny / 2;
+    const float2* xr = x + (size_t)i * N;
+    float2 v[16];
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int ip = t + T * m;
+            const int j = (ip + N / 2) & (N - 1);
+            const int jc = ip < N / 2 ? ip : ip - N;
+            float2 val = cmul(__ldg(&xr[j]), z_factor(z, i, j, ic, jc));
+            if (r) val = cmul(val, __ldg(&tw2N[jc & (2 * N - 1)]));
+            v[m] = val;
+        }
+        fft_n<N, false>(v, sm, t, tw2N);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
+        __syncthreads();
+        // transposed store: At[(2k + r) * ny + i0 + g'] for the RB rows, RB/2 float4 per k
+        const int i0 = blockIdx.x * RB;
+        for (int e = threadIdx.x; e < N * (RB / 2); e += blockDim.x) {
+            const int k = e / (RB / 2), gp = (e % (RB / 2)) * 2;
+            float2 a = smem[gp * (N + N / 16) + pidx(k)];
+            float2 b = smem[(gp + 1) * (N + N / 16) + pidx(k)];
+            *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + i0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- forward cols
+// grid: rows / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
+template <int N, int RG>
+__global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (1024 / (RG * N / 16)) : 1) fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X,
+                                                                const float2* __restrict__ tw2N) {
+    constexpr int T = N / 16;
+    extern __shared__ float2 smem[];
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    float2* sm = smem + g * (N + N / 16);
+    const size_t u = (size_t)blockIdx.x * RG + g;
+    const float2* in = At + u * N;
+    float2* out = X + u * (2 * N);
+    float2 v[16];
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int ip = t + T * m;
+            const int ic = ip < N / 2 ? ip : ip - N;
+            float2 val = __ldg(&in[(ip + N / 2) & (N - 1)]);
+            if (r) val = cmul(val, __ldg(&tw2N[ic & (2 * N - 1)]));
+            v[m] = val;
+        }
+        fft_n<N, false>(v, sm, t, tw2N);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) out[2 * (t + T * m) + r] = v[out_slot<N>(m)];
+    }
+}
+
+// ----------------------------------------------------------------------------- inverse cols
+// grid: gx / RB blocks; rows u of Xh (2N cells along v) -> B[i][u] for the N image rows.
+template <int N, int RB>
+__global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B,
+                                                                int gx, const float2* __restrict__ tw2N) {
+    constexpr int T = N / 16;
+    extern __shared__ float2 smem[];
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    float2* sm = smem + g * (N + N / 16);
+    const size_t u = (size_t)blockIdx.x * RB + g;
+    const float2* in = Xh + u * (2 * N);
+    float2 v[16];
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int k = t + T * m;
+            float2 a = __ldg(&in[k]), b = __ldg(&in[k + N]);
+            v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
+        }
+        fft_n<N, true>(v, sm, t, tw2N);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
+        __syncthreads();
+        // keep outputs m' in [0, N/4) u [3N/4, N): image row i = 2 mm + r + N/2
+        const int u0 = blockIdx.x * RB;
+        for (int e = threadIdx.x; e < (N / 2) * (RB / 2); e += blockDim.x) {
+            const int kk = e / (RB / 2), gp = (e % (RB / 2)) * 2;
+            const int mp = kk < N / 4 ? kk : kk + N / 2;
+            const int mm = kk < N / 4 ? kk : kk - N / 2;
+            const int i = 2 * mm + r + N / 2;
+            float2 a = smem[gp * (N + N / 16) + pidx(mp)];
+            float2 b = smem[(gp + 1) * (N + N / 16) + pidx(mp)];
+            *reinterpret_cast<float4*>(&B[(size_t)i * gx + u0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- inverse rows
+// grid: ny / RG blocks; row i of B (2N cells along u) -> out[i][0 .. N) * conj(Z_p)
+template <int N, int RG>
+__global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (1024 / (RG * N / 16)) : 1) inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out,
+                                                                int ny, ZArgs z, int accumulate, int real_only,
+                                                                const float2* __restrict__ tw2N) {
+    constexpr int T = N / 16;
+    extern __shared__ float2 smem[];
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    float2* sm = smem + g * (N + N / 16);
+    const int i = blockIdx.x * RG + g;
+    const int ic = i - ny / 2;
+    const float2* in = B + (size_t)i * (2 * N);
+    float2* orow = out + (size_t)i * N;
+    float2 v[16];
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int k = t + T * m;
+            float2 a = __ldg(&in[k]), b = __ldg(&in[k + N]);
+            v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
+        }
+        fft_n<N, true>(v, sm, t, tw2N);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int mp = t + T * m;
+            if (mp >= N / 4 && mp < 3 * N / 4) continue;
+            const int mm = mp < N / 4 ? mp : mp - N;
+            const int jc = 2 * mm + r;
+            const int j = jc + N / 2;
+            float2 val = cmulc(v[out_slot<N>(m)], z_factor(z, i, j, ic, jc));
+            if (accumulate) {
+                float2 o = orow[j];
+                val = cadd(val, o);
+            }
+            if (real_only) val.y = 0.f;
+            orow[j] = val;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- launchers
+static ZArgs zargs(const rimo_plan* p, int bin) {
+    ZArgs z;
+    z.dn = p->tab.dn;
+    z.dn_ld = p->nx / 2 + 1;
+    z.gcx = p->tab.gc_x;
+    z.gcy = p->tab.gc_y;
+    z.w_hi = p->bins[bin].w_hi;
+    z.w_lo = p->bins[bin].w_lo;
+    z.div_n = p->prm.n_weight == RIMO_NWEIGHT_DIV_N;
+    return z;
+}
+
+template <int N>
+static constexpr int rows_per_block() { return (N / 16) >= 64 ? 4 : 256 / (N / 16); }
+template <int N>
+static constexpr int groups_per_block() { return (N / 16) >= 256 ? 1 : 256 / (N / 16); }
+
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+    static bool done = false;  // per template instance
+    if (!done) {
+        RIMO_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done = true;
+    }
+}
+
+#define RIMO_DISPATCH_N(N_, CALL)                                                      \
+    switch (N_) {                                                                      \
+        case 64: { constexpr int NN = 64; CALL; } break;                               \
+        case 128: { constexpr int NN = 128; CALL; } break;                             \
+        case 256: { constexpr int NN = 256; CALL; } break;                             \
+        case 512: { constexpr int NN = 512; CALL; } break;                             \
+        case 1024: { constexpr int NN = 1024; CALL; } break;                           \
+        case 2048: { constexpr int NN = 2048; CALL; } break;                           \
+        case 4096: { constexpr int NN = 4096; CALL; } break;                           \
+        default: fail(RIMO_ERR_INVALID_ARG, "unsupported transform length");           \
+    }
+
+template <int N>
+static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
+    constexpr int RB = rows_per_block<N>();
+    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
+    set_smem(fwd_rows_kernel<N, RB>, sm);
+    fwd_rows_kernel<N, RB><<<p->ny / RB, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x);
+}
+
+template <int N>
+static void fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s) {
+    constexpr int RG = groups_per_block<N>();
+    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2);
+    set_smem(fwd_cols_kernel<N, RG>, sm);
+    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 16, sm, s>>>(At, X, p->tab.tw_y);
+}
+
+template <int N>
+static void inv_cols(const rimo_plan* p, const float2* Xh, float2* B, cudaStream_t s) {
+    constexpr int RB = rows_per_block<N>();
+    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
+    set_smem(inv_cols_kernel<N, RB>, sm);
+    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(Xh, B, p->gx, p->tab.tw_y);
+}
+
+template <int N>
+static void inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int acc, int re,
+                     cudaStream_t s) {
+    constexpr int RG = groups_per_block<N>();
+    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2);
+    set_smem(inv_rows_kernel<N, RG>, sm);
+    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 16, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re,
+                                                                p->tab.tw_x);
+}
+
+void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->nx, fwd_rows<NN>(p, bin, x, At, s));
+}
+void launch_fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->ny, fwd_cols<NN>(p, At, X, s));
+}
+void launch_inv_cols(const rimo_plan* p, const float2* Xh, float2* B, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, Xh, B, s));
+}
+void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,
+                     int real_only, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->nx, inv_rows<NN>(p, bin, B, out, accumulate, real_only, s));
+}
+
+}  // namespace rimo

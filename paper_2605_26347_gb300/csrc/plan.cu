@@ -1,0 +1,573 @@
+// Plan creation (stages 1 - 3 of Fig. 3): planning, per-visibility placement on the
+// oversampled grid, uv-tile sort, Fourier blocks (Section 3.2) and the device-side
+// build of the de-gridding matrix G.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+
+#include "internal.h"
+#include "planner.h"
+
+namespace rimo {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void fail(rimo_status s, const std::string& msg) { throw Error{s, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (e == cudaErrorMemoryAllocation)
+            fail(RIMO_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+        fail(RIMO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void* dev_alloc(rimo_plan* p, size_t bytes) {
+    void* ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(RIMO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                               cudaGetErrorString(e));
+    }
+    p->owned.push_back(ptr);
+    return ptr;
+}
+
+template <class T>
+static T* upload(rimo_plan* p, const std::vector<T>& v, cudaStream_t s) {
+    T* d = (T*)dev_alloc(p, v.size() * sizeof(T));
+    if (!v.empty()) RIMO_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Kaiser-Bessel helpers (FP64, host): I0 by its power series; the Fourier transform
+// J sinh(sqrt(beta^2 - (pi J nu)^2)) / (I0(beta) sqrt(beta^2 - (pi J nu)^2)).
+static double bessel_i0(double x) {
+    double q = 0.25 * x * x, term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / ((double)k * k);
+        sum += term;
+        if (term <= 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+static double kb_hat(double nu, int J, double beta) {
+    double a2 = beta * beta - (M_PI * J * nu) * (M_PI * J * nu);
+    double r;
+    if (a2 > 1e-12) r = std::sinh(std::sqrt(a2)) / std::sqrt(a2);
+    else if (a2 < -1e-12) r = std::sin(std::sqrt(-a2)) / std::sqrt(-a2);
+    else r = 1.0;
+    return J * r / bessel_i0(beta);
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static void validate(const rimo_plan_params& q) {
+    auto bad = [](const std::string& m) { fail(RIMO_ERR_INVALID_ARG, m); };
+    if (!is_pow2(q.nx) || !is_pow2(q.ny) || q.nx < 64 || q.ny < 64 || q.nx > 4096 || q.ny > 4096)
+        bad("nx and ny must be powers of two in [64, 4096]");
+    if (!(q.fov_x > 0) || !(q.fov_y > 0) || q.fov_x * q.fov_x + q.fov_y * q.fov_y >= 0.99)
+        bad("fov_x and fov_y must be positive and keep (2 fov)^2 / 4 summed below 1");
+    if (q.oversampling != 2) bad("oversampling must be 2");
+    if (q.kb_support < 3 || q.kb_support > 11 || (q.kb_support & 1) == 0)
+        bad("kb_support must be odd in [3, 11]");
+    if (q.max_wsupport < 1 || q.max_wsupport > 9 || (q.max_wsupport & 1) == 0)
+        bad("max_wsupport must be odd in [1, 9]");
+    if (!(q.w_norm_frac > 0) || q.w_norm_frac > 1) bad("w_norm_frac must be in (0, 1]");
+    if (q.n_wbins < 0 || q.n_wbins > 4096) bad("n_wbins must be in [0, 4096]");
+    if (q.mode < 0 || q.mode > 4) bad("mode must be a rimo_mode");
+    if (q.n_weight < 0 || q.n_weight > 1) bad("n_weight must be 0 or 1");
+    if (q.plan_fraction <= 0 || q.plan_fraction > 1) bad("plan_fraction must be in (0, 1]");
+    if (q.wkernel_L != 0 && (!is_pow2(q.wkernel_L) || q.wkernel_L < 16 || q.wkernel_L > 128))
+        bad("wkernel_L must be 0 or a power of two in [16, 128]");
+    if (q.tile_size != 0 && q.tile_size != 32 && q.tile_size != 64) bad("tile_size must be 0, 32 or 64");
+    if (q.kb_beta < 0) bad("kb_beta must be >= 0");
+}
+
+static planner::Params planner_params(const rimo_plan_params& q) {
+    planner::Params pr;
+    pr.nx = q.nx;
+    pr.ny = q.ny;
+    pr.J = q.kb_support;
+    pr.kg.L = q.wkernel_L ? q.wkernel_L
+                          : std::max(32, 1 << (int)std::ceil(std::log2(4.0 * q.max_wsupport)));
+    pr.kg.max_wsupport = q.max_wsupport;
+    pr.kg.fov_x = q.fov_x;
+    pr.kg.fov_y = q.fov_y;
+    pr.kg.eta = q.w_norm_frac;
+    pr.kg.literal = q.taper_literal != 0;
+    pr.seed = q.seed;
+    pr.plan_fraction = q.plan_fraction;
+    pr.n_wbins = q.n_wbins;
+    pr.mode = q.mode;
+    pr.budget = q.mem_budget_bytes;
+    return pr;
+}
+
+static void fill_estimate(rimo_plan_info* info, const planner::Choice& ch, int64_t M, int L) {
+    info->M = M;
+    info->P = ch.P;
+    info->mode = ch.mode;
+    info->p_star = ch.p_star;
+    info->subset = ch.subset;
+    info->est_m_g = ch.est_m_g;
+    info->est_cost = ch.est_cost;
+    info->wsclean_p = ch.wsclean;
+    info->wkernel_L = L;
+}
+
+// ---------------------------------------------------------------------------
+// Device tables of one plan.
+static void build_tables(rimo_plan* p, cudaStream_t s) {
+    const int nx = p->nx, ny = p->ny, J = p->J, L = p->L;
+    auto twiddles = [](int N) {
+        std::vector<float2> t(2 * N);
+        for (int k = 0; k < 2 * N; ++k) {
+            double a = -2.0 * M_PI * (double)k / (2.0 * N);
+            t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        return t;
+    };
+    p->tab.tw_x = upload(p, twiddles(nx), s);
+    p->tab.tw_y = upload(p, twiddles(ny), s);
+    auto gc = [&](int n) {
+        std::vector<float> g(n);
+        for (int j = 0; j < n; ++j) g[j] = (float)(1.0 / kb_hat((double)(j - n / 2) / (2.0 * n), J, p->beta));
+        return g;
+    };
+    p->tab.gc_x = upload(p, gc(nx), s);
+    p->tab.gc_y = upload(p, gc(ny), s);
+    const int qx = nx / 2 + 1, qy = ny / 2 + 1;
+    std::vector<float2> dnq((size_t)qx * qy);
+    const double dl = p->prm.fov_x / nx, dm = p->prm.fov_y / ny;
+    for (int i = 0; i < qy; ++i)
+        for (int j = 0; j < qx; ++j) {
+            double d = planner::dn(j * dl, i * dm);
+            float hi = (float)d;
+            dnq[(size_t)i * qx + j] = make_float2(hi, (float)(d - (double)hi));
+        }
+    p->tab.dn = upload(p, dnq, s);
+    // KB(t) = sum_k e_k rho^k, rho = 1 - (2t/J)^2, e_k = (beta^2/4)^k / (k!)^2 / I0(beta)
+    std::vector<float> coef;
+    {
+        double i0b = bessel_i0(p->beta), q0 = 0.25 * p->beta * p->beta, d = 1.0;
+        for (int k = 0; k < 96; ++k) {
+            if (k > 0) d *= q0 / ((double)k * k);
+            coef.push_back((float)(d / i0b));
+            if (k > 4 && d / i0b < 1e-13) break;
+        }
+    }
+    p->tab.kb_nterm = (int)coef.size();
+    p->tab.kb_coef = upload(p, coef, s);
+    // residual w-kernel sampling grid over twice the field of view (Section 3.1, Fig. 1)
+    std::vector<float> wdn((size_t)L * L), tx(L), ty(L);
+    auto taper = [](double lam, double fov) {
+        double a = std::fabs(lam), half = 0.5 * fov;
+        return a <= half ? 1.0 : 0.54 + 0.46 * std::cos(M_PI * (a - half) / half);
+    };
+    for (int a = 0; a < L; ++a) {
+        double lam = (a - L / 2) * (2.0 * p->prm.fov_x / L);
+        double mu = (a - L / 2) * (2.0 * p->prm.fov_y / L);
+        tx[a] = (float)taper(lam, p->prm.fov_x);
+        ty[a] = (float)taper(mu, p->prm.fov_y);
+    }
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b) {
+            double lam = (a - L / 2) * (2.0 * p->prm.fov_x / L);
+            double mu = (b - L / 2) * (2.0 * p->prm.fov_y / L);
+            wdn[(size_t)a * L + b] = (float)planner::dn(lam, mu);
+        }
+    const int ns = 2 * p->hmax + 1;
+    std::vector<float2> E((size_t)L * ns);
+    for (int a = 0; a < L; ++a)
+        for (int t = 0; t < ns; ++t) {
+            double ang = 2.0 * M_PI * (double)(t - p->hmax) * (double)(a - L / 2) / (double)L;
+            E[(size_t)a * ns + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+    p->tab.wk_dn = upload(p, wdn, s);
+    p->tab.wk_tau_x = upload(p, tx, s);
+    p->tab.wk_tau_y = upload(p, ty, s);
+    p->tab.wk_E = upload(p, E, s);
+}
+
+// ---------------------------------------------------------------------------
+static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q, cudaStream_t s,
+                        rimo_plan* p) {
+    validate(q);
+    p->prm = q;
+    p->nx = q.nx;
+    p->ny = q.ny;
+    p->gx = 2 * q.nx;
+    p->gy = 2 * q.ny;
+    p->J = q.kb_support;
+    p->beta = q.kb_beta > 0 ? q.kb_beta : 2.34 * q.kb_support;
+    p->TS = q.tile_size ? q.tile_size : 64;
+    p->M = M;
+    planner::Params pr = planner_params(q);
+    p->L = pr.kg.L;
+    p->hmax = q.max_wsupport / 2;
+
+    // ---- stage 1: planning on the subset (Section 3.4)
+    planner::Choice ch = planner::choose(uvw, M, pr);
+    fill_estimate(&p->info, ch, M, p->L);
+    p->P = ch.P;
+    p->mode = ch.mode;
+    if (p->mode == RIMO_MODE_SURROGATE || p->mode == RIMO_MODE_ONTHEFLY)
+        fail(RIMO_ERR_UNSUPPORTED, "on-the-fly kernel modes are created with their own entry point");
+    if (p->mode == RIMO_MODE_HOLOGRAPHIC) p->holographic = false;  // G first, H on request
+
+    // ---- w-bins on the subset, every visibility to its nearest bin (Section 3.1)
+    std::vector<double> w_sub = planner::subset_w(uvw, M, q.seed, q.plan_fraction);
+    p->w_stack = planner::kmeans1d(w_sub, p->P, 100);
+    std::vector<int32_t> bin(M);
+    planner::nearest_all(uvw + 2, M, 3, p->w_stack, bin.data());
+    std::vector<double> wr(M);
+    double wr_max = 0.0;
+    for (int64_t k = 0; k < M; ++k) {
+        wr[k] = uvw[3 * k + 2] - p->w_stack[bin[k]];
+        wr_max = std::max(wr_max, std::fabs(wr[k]));
+    }
+    std::vector<int32_t> tab = planner::support_table(wr_max, pr.kg);
+    p->info.wr_max = wr_max;
+    for (int i = 0; i < 64; ++i) p->info.support_table[i] = tab[i];
+
+    // ---- placement on the oversampled grid: u~ = u * (2 fov_x), one FP64 multiply
+    const int J = p->J, TS = p->TS, gx = p->gx, gy = p->gy;
+    const int ntu = gx / TS, ntv = gy / TS;
+    std::vector<int32_t> sw(M), g0(M), h0(M);
+    std::vector<float> phiu(M), phiv(M);
+    int max_sw = 1;
+    planner::parallel_for(M, [&](int64_t b, int64_t e) {
+        for (int64_t k = b; k < e; ++k) {
+            int Sw = tab[planner::support_bin(std::fabs(wr[k]), wr_max)];
+            sw[k] = Sw;
+            int h = (Sw - 1) / 2;
+            double tu = uvw[3 * k + 0] * (2.0 * q.fov_x) - J / 2.0;
+            double tv = uvw[3 * k + 1] * (2.0 * q.fov_y) - J / 2.0;
+            double fu = std::floor(tu), fv = std::floor(tv);
+            phiu[k] = (float)(tu - fu);
+            phiv[k] = (float)(tv - fv);
+            int64_t a = (int64_t)fu + 1 - h, c = (int64_t)fv + 1 - h;
+            a %= gx; if (a < 0) a += gx;
+            c %= gy; if (c < 0) c += gy;
+            g0[k] = (int32_t)a;
+            h0[k] = (int32_t)c;
+        }
+    }, 1 << 16);
+    for (int64_t k = 0; k < M; ++k) max_sw = std::max(max_sw, sw[k]);
+    p->max_S = max_sw + J - 1;
+    p->H = p->max_S - 1;
+    p->PW = TS + p->H;
+    p->info.max_tile = p->max_S;
+
+    // ---- sort by (bin, uv-tile): stable counting sort, bins first then tiles per bin
+    const int P = p->P;
+    std::vector<int64_t> bstart(P + 1, 0);
+    for (int64_t k = 0; k < M; ++k) bstart[bin[k] + 1]++;
+    for (int b = 0; b < P; ++b) bstart[b + 1] += bstart[b];
+    std::vector<int32_t> by_bin(M);
+    {
+        std::vector<int64_t> cur(bstart.begin(), bstart.end() - 1);
+        for (int64_t k = 0; k < M; ++k) by_bin[cur[bin[k]]++] = (int32_t)k;
+    }
+    std::vector<int32_t> order(M);
+    const int64_t ntile = (int64_t)ntu * ntv;
+    std::vector<std::vector<int64_t>> tstart(P);
+    planner::parallel_for(P, [&](int64_t b0, int64_t b1) {
+        for (int64_t b = b0; b < b1; ++b) {
+            auto& st = tstart[b];
+            st.assign(ntile + 1, 0);
+            for (int64_t i = bstart[b]; i < bstart[b + 1]; ++i) {
+                int k = by_bin[i];
+                st[(int64_t)(g0[k] / TS) * ntv + h0[k] / TS + 1]++;
+            }
+            for (int64_t t = 0; t < ntile; ++t) st[t + 1] += st[t];
+            std::vector<int64_t> cur(st.begin(), st.end() - 1);
+            for (int64_t i = bstart[b]; i < bstart[b + 1]; ++i) {
+                int k = by_bin[i];
+                int64_t t = (int64_t)(g0[k] / TS) * ntv + h0[k] / TS;
+                order[bstart[b] + cur[t]++] = k;
+            }
+        }
+    }, 1);
+    std::vector<int32_t>().swap(by_bin);
+
+    // ---- active tiles, phases, Fourier blocks by radial sweep (Section 3.2)
+    struct T {
+        int32_t tu, tv;
+        int64_t vb, ve;
+        double r, bytes;
+    };
+    std::vector<std::vector<T>> tl(P);
+    double total_bytes = 0.0;
+    for (int b = 0; b < P; ++b) {
+        for (int64_t t = 0; t < ntile; ++t) {
+            int64_t vb = tstart[b][t], ve = tstart[b][t + 1];
+            if (ve == vb) continue;
+            T x;
+            x.tu = (int32_t)(t / ntv);
+            x.tv = (int32_t)(t % ntv);
+            x.vb = bstart[b] + vb;
+            x.ve = bstart[b] + ve;
+            double cu = x.tu * TS + 0.5 * TS, cv = x.tv * TS + 0.5 * TS;
+            if (cu >= gx / 2) cu -= gx;
+            if (cv >= gy / 2) cv -= gy;
+            x.r = std::sqrt(cu * cu + cv * cv);
+            x.bytes = 0;
+            for (int64_t i = x.vb; i < x.ve; ++i) {
+                int64_t S = sw[order[i]] + J - 1;
+                x.bytes += 8.0 * (double)(S * S + ((S * S) & 1));
+            }
+            total_bytes += x.bytes;
+            tl[b].push_back(x);
+        }
+    }
+    tstart.clear();
+    double limit = q.block_bytes_max > 0 ? (double)q.block_bytes_max : 8.0 * 1073741824.0;
+    if (q.n_blocks > 0) limit = std::ceil(total_bytes / q.n_blocks);
+    limit = std::max(limit, std::ceil(total_bytes / 200.0));
+    std::vector<VisMeta> meta(M);
+    std::vector<float> wr_s(M), pu_s(M), pv_s(M);
+    p->bins.assign(P, BinRange());
+    p->block_bytes.clear();
+    int64_t K = 0;
+    for (int b = 0; b < P; ++b) {
+        auto& v = tl[b];
+        std::vector<int> rad(v.size());
+        std::iota(rad.begin(), rad.end(), 0);
+        std::stable_sort(rad.begin(), rad.end(), [&](int x, int y) { return v[x].r < v[y].r; });
+        double cur = 0.0;
+        int64_t off = 0;
+        bool open = false;
+        for (int id : rad) {
+            if (!open || (cur + v[id].bytes > limit && cur > 0)) {
+                p->block_bytes.push_back(0);
+                cur = 0.0;
+                off = 0;
+                open = true;
+            }
+            int blk = (int)p->block_bytes.size() - 1;
+            for (int64_t i = v[id].vb; i < v[id].ve; ++i) {
+                int k = order[i];
+                int S = sw[k] + J - 1;
+                int du = g0[k] - v[id].tu * TS, dv = h0[k] - v[id].tv * TS;
+                meta[i].off = off;
+                meta[i].orig = (uint32_t)k;
+                meta[i].pos = (uint32_t)du | ((uint32_t)dv << 8) | ((uint32_t)S << 16) |
+                              ((uint32_t)blk << 24);
+                int64_t n = (int64_t)S * S;
+                off += n + (n & 1);
+                K += n;
+                wr_s[i] = (float)wr[k];
+                pu_s[i] = phiu[k];
+                pv_s[i] = phiv[k];
+            }
+            cur += v[id].bytes;
+            p->block_bytes.back() = off * 8;
+        }
+        p->bins[b].vb = bstart[b];
+        p->bins[b].ve = bstart[b + 1];
+        p->bins[b].w = p->w_stack[b];
+        p->bins[b].w_hi = (float)p->w_stack[b];
+        p->bins[b].w_lo = (float)(p->w_stack[b] - (double)p->bins[b].w_hi);
+    }
+    if (p->block_bytes.size() > 255) fail(RIMO_ERR_INVALID_ARG, "more than 255 Fourier blocks");
+    // tile lists per (bin, phase), heaviest first for load balance
+    p->tiles_host.clear();
+    int n_active = 0;
+    for (int b = 0; b < P; ++b) {
+        for (int ph = 0; ph < 4; ++ph) {
+            p->bins[b].tile_off[ph] = (int32_t)p->tiles_host.size();
+            std::vector<const T*> sel;
+            for (const auto& x : tl[b])
+                if (((x.tu & 1) * 2 + (x.tv & 1)) == ph) sel.push_back(&x);
+            std::stable_sort(sel.begin(), sel.end(), [](const T* a, const T* c) {
+                return (a->ve - a->vb) > (c->ve - c->vb);
+            });
+            for (const T* x : sel) p->tiles_host.push_back(TileDesc{x->tu, x->tv, x->vb, x->ve});
+        }
+        p->bins[b].tile_off[4] = (int32_t)p->tiles_host.size();
+        n_active += (int)tl[b].size();
+    }
+
+    // ---- caller-order host copies
+    p->bins_user = bin;
+    p->sw_user = sw;
+    p->inv_perm.assign(M, 0);
+    for (int64_t i = 0; i < M; ++i) p->inv_perm[order[i]] = (int32_t)i;
+
+    // ---- device
+    build_tables(p, s);
+    p->d_meta = upload(p, meta, s);
+    p->d_tiles = upload(p, p->tiles_host, s);
+    p->d_wr = upload(p, wr_s, s);
+    p->d_phiu = upload(p, pu_s, s);
+    p->d_phiv = upload(p, pv_s, s);
+    int64_t gbytes = 0;
+    for (int64_t bb : p->block_bytes) {
+        p->d_gblocks.push_back((float2*)dev_alloc(p, (size_t)std::max<int64_t>(bb, 16)));
+        gbytes += bb;
+    }
+    std::vector<float2*> ptrs(p->d_gblocks);
+    p->d_gblock_ptrs = upload(p, ptrs, s);
+    const size_t grid_elems = (size_t)gx * gy;
+    p->d_X = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
+    p->d_Xh = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
+    p->d_AB = (float2*)dev_alloc(p, (size_t)2 * p->nx * p->ny * sizeof(float2));
+    p->d_delta = (float2*)dev_alloc(p, (size_t)p->nx * p->ny * sizeof(float2));
+    RIMO_CUDA(cudaMemsetAsync(p->d_delta, 0, (size_t)p->nx * p->ny * sizeof(float2), s));
+    float2 one = make_float2(1.f, 0.f);
+    RIMO_CUDA(cudaMemcpyAsync(p->d_delta + (size_t)(p->ny / 2) * p->nx + p->nx / 2, &one,
+                              sizeof(float2), cudaMemcpyHostToDevice, s));
+    p->info.K = K;
+    p->info.g_bytes = gbytes + (int64_t)M * (int64_t)sizeof(VisMeta);
+    p->info.scratch_bytes = (int64_t)(2 * grid_elems + 3 * (size_t)p->nx * p->ny) * 8;
+    p->info.n_blocks = (int32_t)p->block_bytes.size();
+    p->info.n_tiles = n_active;
+
+    // ---- stage 3: precompute G on the device
+    launch_gbuild(p, s);
+    RIMO_CUDA(cudaGetLastError());
+    RIMO_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace rimo
+
+using namespace rimo;
+
+extern "C" {
+
+void rimo_plan_params_default(rimo_plan_params* q, int32_t nx, int32_t ny, double fov_x,
+                              double fov_y) {
+    std::memset(q, 0, sizeof(*q));
+    q->nx = nx;
+    q->ny = ny;
+    q->fov_x = fov_x;
+    q->fov_y = fov_y;
+    q->oversampling = 2;
+    q->kb_support = 7;
+    q->kb_beta = 0.0;
+    q->max_wsupport = 9;
+    q->w_norm_frac = 0.9999;
+    q->plan_fraction = 0.01;
+    q->seed = 12345;
+    q->mode = RIMO_MODE_AUTO;
+}
+
+rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_params* q,
+                               rimo_plan_info* info) {
+    try {
+        if (!uvw || M <= 0 || !q || !info) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
+        validate(*q);
+        planner::Params pr = planner_params(*q);
+        planner::Choice ch = planner::choose(uvw, M, pr);
+        std::memset(info, 0, sizeof(*info));
+        fill_estimate(info, ch, M, pr.kg.L);
+        return RIMO_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return RIMO_ERR_OOM;
+    }
+}
+
+rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_params* q,
+                             void* stream, rimo_plan_t* out) {
+    if (out) *out = nullptr;
+    rimo_plan* p = nullptr;
+    try {
+        if (!uvw || M <= 0 || !q || !out) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
+        if (M > 2000000000LL) fail(RIMO_ERR_INVALID_ARG, "M above 2e9 visibilities");
+        p = new rimo_plan();
+        create_plan(uvw, M, *q, (cudaStream_t)stream, p);
+        *out = p;
+        return RIMO_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        rimo_plan_destroy(p);
+        return e.status;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        rimo_plan_destroy(p);
+        return RIMO_ERR_OOM;
+    }
+}
+
+rimo_status rimo_plan_destroy(rimo_plan_t p) {
+    if (!p) return RIMO_OK;
+    for (void* ptr : p->owned) cudaFree(ptr);
+    delete p;
+    return RIMO_OK;
+}
+
+rimo_status rimo_plan_info_get(rimo_plan_t p, rimo_plan_info* info) {
+    if (!p || !info) {
+        set_last_error("null plan or info");
+        return RIMO_ERR_INVALID_ARG;
+    }
+    *info = p->info;
+    return RIMO_OK;
+}
+
+rimo_status rimo_plan_get_bins(rimo_plan_t p, double* w_stack, int32_t* bins, int32_t* s_w) {
+    if (!p) {
+        set_last_error("null plan");
+        return RIMO_ERR_INVALID_ARG;
+    }
+    if (w_stack) std::memcpy(w_stack, p->w_stack.data(), p->w_stack.size() * sizeof(double));
+    if (bins) std::memcpy(bins, p->bins_user.data(), p->bins_user.size() * sizeof(int32_t));
+    if (s_w) std::memcpy(s_w, p->sw_user.data(), p->sw_user.size() * sizeof(int32_t));
+    return RIMO_OK;
+}
+
+rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, int32_t* g0,
+                                int32_t* h0, int32_t* S, rimo_cfloat* taps, void* stream) {
+    try {
+        if (!p || (n > 0 && (!idx || !g0 || !h0 || !S || !taps)) || n < 0)
+            fail(RIMO_ERR_INVALID_ARG, "null pointer or n < 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        for (int64_t q = 0; q < n; ++q) {
+            if (idx[q] < 0 || idx[q] >= p->M) fail(RIMO_ERR_INVALID_ARG, "visibility index out of range");
+            int64_t i = p->inv_perm[idx[q]];
+            VisMeta m;
+            RIMO_CUDA(cudaMemcpyAsync(&m, p->d_meta + i, sizeof(m), cudaMemcpyDeviceToHost, s));
+            RIMO_CUDA(cudaStreamSynchronize(s));
+            int du = m.pos & 255, dv = (m.pos >> 8) & 255, Sq = (m.pos >> 16) & 255, blk = m.pos >> 24;
+            // the tile containing sorted position i
+            int b = p->bins_user[idx[q]];
+            int tu = -1, tv = -1;
+            for (int t = p->bins[b].tile_off[0]; t < p->bins[b].tile_off[4]; ++t)
+                if (p->tiles_host[t].vb <= i && i < p->tiles_host[t].ve) {
+                    tu = p->tiles_host[t].tu;
+                    tv = p->tiles_host[t].tv;
+                }
+            g0[q] = tu * p->TS + du;
+            h0[q] = tv * p->TS + dv;
+            S[q] = Sq;
+            RIMO_CUDA(cudaMemcpyAsync(taps + q * 361, p->d_gblocks[blk] + m.off,
+                                      (size_t)Sq * Sq * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        }
+        RIMO_CUDA(cudaStreamSynchronize(s));
+        return RIMO_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        return e.status;
+    }
+}
+
+const char* rimo_last_error(void) { return g_last_error.c_str(); }
+
+const char* rimo_version(void) { return "rimo 0.1 (sm_103a)"; }
+
+}  // extern "C"

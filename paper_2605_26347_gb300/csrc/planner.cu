@@ -1,0 +1,309 @@
+// Host-side planning: w-bins by k-means (Section 3.1), supports from logical kernels
+// (Section 3.2 footnote), memory and cost models (Eq. 9, Eq. 10) and the decision
+// tree of Section 3.4 / Fig. 2.  Plain C++ on the host, FP64, multi-threaded.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <thread>
+
+#include "planner.h"
+
+namespace rimo {
+namespace planner {
+
+static const int CANDIDATE_P[] = {1,  2,  3,  4,  5,  6,  8,  10,  12,  16,  20,
+                                  24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256};
+
+int hw_threads() {
+    unsigned n = std::thread::hardware_concurrency();
+    return n == 0 ? 1 : (int)std::min(n, 64u);
+}
+
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f, int64_t min_chunk) {
+    int T = hw_threads();
+    int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(T, n / std::max<int64_t>(1, min_chunk)));
+    if (chunks <= 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t step = (n + chunks - 1) / chunks;
+    for (int64_t c = 0; c < chunks; ++c) {
+        int64_t b = c * step, e = std::min(n, b + step);
+        if (b < e) th.emplace_back(f, b, e);
+    }
+    for (auto& t : th) t.join();
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014).
+static inline uint64_t splitmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+std::vector<double> subset_w(const double* uvw, int64_t M, uint64_t seed, double fraction) {
+    double frac = std::max(fraction, std::min(1.0, 4096.0 / (double)std::max<int64_t>(M, 1)));
+    std::vector<double> out;
+    if (frac >= 1.0) {
+        out.resize(M);
+        for (int64_t k = 0; k < M; ++k) out[k] = uvw[3 * k + 2];
+        return out;
+    }
+    out.reserve((size_t)(M * frac * 1.1) + 16);
+    const uint64_t golden = 0x9E3779B97F4A7C15ull;
+    for (int64_t k = 0; k < M; ++k) {
+        uint64_t st = seed + (uint64_t)(k + 1) * golden;
+        double u = (double)(splitmix64(st) >> 11) * 0x1.0p-53;
+        if (u < frac) out.push_back(uvw[3 * k + 2]);
+    }
+    return out;
+}
+
+// argmin_p |w - c_p| with ties to the lowest index (c ascending).
+static inline int nearest_sorted(double w, const double* c, int P) {
+    int lo = 0, hi = P;  // first index with c >= w
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (c[mid] < w) lo = mid + 1; else hi = mid;
+    }
+    int q = lo, best;
+    if (q == 0) best = 0;
+    else if (q == P) best = P - 1;
+    else best = (std::fabs(w - c[q - 1]) <= std::fabs(w - c[q])) ? q - 1 : q;
+    while (best > 0 && c[best - 1] == c[best]) --best;
+    return best;
+}
+
+static inline int nearest_scan(double w, const double* c, int P) {
+    int best = 0;
+    double bd = std::fabs(w - c[0]);
+    for (int p = 1; p < P; ++p) {
+        double d = std::fabs(w - c[p]);
+        if (d < bd) { bd = d; best = p; }
+    }
+    return best;
+}
+
+void nearest_all(const double* w, int64_t n, int64_t stride, const std::vector<double>& c,
+                 int32_t* lab) {
+    int P = (int)c.size();
+    bool sorted = std::is_sorted(c.begin(), c.end());
+    parallel_for(n, [&](int64_t b, int64_t e) {
+        for (int64_t k = b; k < e; ++k) {
+            double wk = w[k * stride];
+            lab[k] = sorted ? nearest_sorted(wk, c.data(), P) : nearest_scan(wk, c.data(), P);
+        }
+    }, 1 << 14);
+}
+
+std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter) {
+    int64_t n = (int64_t)w.size();
+    std::vector<double> ws(w);
+    std::sort(ws.begin(), ws.end());
+    std::vector<double> c(P);
+    for (int p = 0; p < P; ++p) {
+        int64_t idx = (int64_t)(((p + 0.5) * (double)n) / (double)P);
+        c[p] = ws[std::min<int64_t>(n - 1, idx)];
+    }
+    std::vector<int32_t> lab(n), nl(n);
+    nearest_all(w.data(), n, 1, c, lab.data());
+    std::vector<double> sum(P);
+    std::vector<int64_t> cnt(P);
+    for (int it = 0; it < max_iter; ++it) {
+        std::fill(sum.begin(), sum.end(), 0.0);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int64_t k = 0; k < n; ++k) { sum[lab[k]] += w[k]; cnt[lab[k]]++; }
+        for (int p = 0; p < P; ++p)
+            if (cnt[p]) c[p] = sum[p] / (double)cnt[p];
+        nearest_all(w.data(), n, 1, c, nl.data());
+        if (nl == lab) break;
+        lab.swap(nl);
+    }
+    std::sort(c.begin(), c.end());
+    return c;
+}
+
+// sqrt(1 - l^2 - m^2) - 1 in the cancellation-free form -s / (1 + sqrt(1 - s)).
+double dn(double l, double m) {
+    double s = l * l + m * m;
+    return -s / (1.0 + std::sqrt(1.0 - s));
+}
+
+double wsclean_bound(const double* uvw, int64_t M, double fov_x, double fov_y) {
+    double lo = 0, hi = 0;
+    for (int64_t k = 0; k < M; ++k) {
+        double w = uvw[3 * k + 2];
+        if (k == 0 || w < lo) lo = w;
+        if (k == 0 || w > hi) hi = w;
+    }
+    return 2.0 * M_PI * (hi - lo) * (-dn(0.5 * fov_x, 0.5 * fov_y));
+}
+
+static double taper(double lam, double fov) {
+    double a = std::fabs(lam), half = 0.5 * fov;
+    if (a <= half) return 1.0;
+    return 0.54 + 0.46 * std::cos(M_PI * (a - half) / half);
+}
+
+// Support of the residual kernel at offset w_r: smallest odd s whose centred s x s taps
+// keep >= eta of the l2 norm of all L x L taps (norm by Parseval from the samples).
+int support_at(double w_r, const KernelGeom& g) {
+    int L = g.L, hm = g.max_wsupport / 2, ns = 2 * hm + 1;
+    std::vector<std::complex<double>> c((size_t)L * L);
+    double tot = 0.0;
+    for (int a = 0; a < L; ++a) {
+        double lam = (a - L / 2) * (2.0 * g.fov_x / L);
+        double ta = taper(lam, g.fov_x);
+        for (int b = 0; b < L; ++b) {
+            double mu = (b - L / 2) * (2.0 * g.fov_y / L);
+            double tb = taper(mu, g.fov_y);
+            double ph = -2.0 * M_PI * w_r * dn(lam, mu);
+            std::complex<double> ch(std::cos(ph), std::sin(ph));
+            std::complex<double> v = g.literal ? (ta * tb) * ch : 1.0 + (ta * tb) * (ch - 1.0);
+            c[(size_t)a * L + b] = v;
+            tot += std::norm(v);
+        }
+    }
+    tot /= (double)L * L;  // sum_t |K(t)|^2 = (1/L^2) sum |c|^2
+    // central taps K(tx, ty), |t| <= hm: row pass over a, then column pass over b
+    std::vector<std::complex<double>> E((size_t)L * ns), R((size_t)L * ns), K((size_t)ns * ns);
+    for (int a = 0; a < L; ++a)
+        for (int s = 0; s < ns; ++s) {
+            double ang = 2.0 * M_PI * (double)(s - hm) * (double)(a - L / 2) / (double)L;
+            E[(size_t)a * ns + s] = std::complex<double>(std::cos(ang), std::sin(ang));
+        }
+    for (int b = 0; b < L; ++b)
+        for (int s = 0; s < ns; ++s) {
+            std::complex<double> acc = 0.0;
+            for (int a = 0; a < L; ++a) acc += c[(size_t)a * L + b] * E[(size_t)a * ns + s];
+            R[(size_t)b * ns + s] = acc;
+        }
+    for (int sx = 0; sx < ns; ++sx)
+        for (int sy = 0; sy < ns; ++sy) {
+            std::complex<double> acc = 0.0;
+            for (int b = 0; b < L; ++b) acc += R[(size_t)b * ns + sx] * E[(size_t)b * ns + sy];
+            K[(size_t)sx * ns + sy] = acc / ((double)L * L);
+        }
+    double total = std::sqrt(tot);
+    for (int s = 1; s <= g.max_wsupport; s += 2) {
+        int h = s / 2;
+        double e = 0.0;
+        for (int x = hm - h; x <= hm + h; ++x)
+            for (int y = hm - h; y <= hm + h; ++y) e += std::norm(K[(size_t)x * ns + y]);
+        if (std::sqrt(e) >= g.eta * total) return s;
+    }
+    return g.max_wsupport;
+}
+
+std::vector<int32_t> support_table(double wr_max, const KernelGeom& g) {
+    std::vector<int32_t> tab(N_SUPPORT_BINS, 1);
+    if (wr_max <= 0.0) return tab;
+    double step = wr_max / N_SUPPORT_BINS;
+    std::vector<int32_t> raw(N_SUPPORT_BINS);
+    parallel_for(N_SUPPORT_BINS, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) raw[q] = support_at((double)(q + 1) * step, g);
+    }, 1);
+    int run = 1;
+    for (int q = 0; q < N_SUPPORT_BINS; ++q) { run = std::max(run, raw[q]); tab[q] = run; }
+    return tab;
+}
+
+int support_bin(double abs_wr, double wr_max) {
+    if (wr_max <= 0.0) return 0;
+    double step = wr_max / N_SUPPORT_BINS;
+    double q = std::floor(abs_wr / step);
+    return q >= N_SUPPORT_BINS - 1 ? N_SUPPORT_BINS - 1 : (int)q;
+}
+
+static ModelPoint model_for_P(const std::vector<double>& w_sub, int64_t M, int P,
+                              const Params& pr) {
+    std::vector<double> c = kmeans1d(w_sub, P, 100);
+    int64_t n = (int64_t)w_sub.size();
+    std::vector<int32_t> lab(n);
+    nearest_all(w_sub.data(), n, 1, c, lab.data());
+    std::vector<double> wr(n);
+    double wr_max = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        wr[k] = w_sub[k] - c[lab[k]];
+        wr_max = std::max(wr_max, std::fabs(wr[k]));
+    }
+    std::vector<int32_t> tab = support_table(wr_max, pr.kg);
+    int64_t s2 = 0, s2p = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t S = tab[support_bin(std::fabs(wr[k]), wr_max)] + pr.J - 1;
+        s2 += S * S;
+        s2p += (S * S) + ((S * S) & 1);
+    }
+    double scale = (double)M / (double)n;
+    ModelPoint mp;
+    mp.P = P;
+    mp.K = (double)s2 * scale;
+    double KP = (double)s2p * scale;
+    mp.m_G = 8.0 * KP + (double)META_BYTES_PER_VIS * (double)M;
+    double Np = 4.0 * (double)pr.nx * (double)pr.ny;
+    mp.cost = 2.0 * (10.0 * Np * std::log2(std::sqrt(Np)) * (double)P + 6.0 * mp.K);
+    return mp;
+}
+
+Choice choose(const double* uvw, int64_t M, const Params& pr) {
+    Choice ch;
+    std::vector<double> w_sub = subset_w(uvw, M, pr.seed, pr.plan_fraction);
+    ch.subset = (int64_t)w_sub.size();
+    ch.wsclean = wsclean_bound(uvw, M, pr.kg.fov_x, pr.kg.fov_y);
+    std::vector<int> cands;
+    if (pr.n_wbins > 0) {
+        cands.push_back(pr.n_wbins);
+    } else {
+        int pmax = std::max(1, (int)std::ceil(ch.wsclean));
+        for (int p : CANDIDATE_P)
+            if (p <= std::max(pmax, 1) && p <= std::max<int64_t>(1, ch.subset)) cands.push_back(p);
+    }
+    for (int p : cands) ch.models.push_back(model_for_P(w_sub, M, p, pr));
+    const ModelPoint* best = &ch.models[0];
+    for (const auto& m : ch.models)
+        if (m.cost < best->cost || (m.cost == best->cost && m.P < best->P)) best = &m;
+    ch.p_star = best->P;
+    ch.est_m_g = best->m_G;
+    ch.est_cost = best->cost;
+    double budget = (double)pr.budget;
+    if (pr.mode != RIMO_MODE_AUTO) {
+        ch.P = best->P;
+        ch.mode = pr.mode;
+        return ch;
+    }
+    if (pr.budget <= 0 || best->m_G <= budget) {
+        ch.P = best->P;
+        ch.mode = RIMO_MODE_STORED_G;
+        return ch;
+    }
+    const ModelPoint* pick = nullptr;
+    for (const auto& m : ch.models) {
+        if (m.m_G > budget) continue;
+        if (!pick) { pick = &m; continue; }
+        int d = std::abs(m.P - best->P), dp = std::abs(pick->P - best->P);
+        if (d < dp || (d == dp && m.P < pick->P)) pick = &m;
+    }
+    if (pick) {
+        ch.P = pick->P;
+        ch.mode = RIMO_MODE_STORED_G;
+        ch.est_m_g = pick->m_G;
+        ch.est_cost = pick->cost;
+        return ch;
+    }
+    double mmin = ch.models[0].m_G;
+    for (const auto& m : ch.models) mmin = std::min(mmin, m.m_G);
+    const ModelPoint* st = nullptr;
+    for (const auto& m : ch.models)
+        if (m.m_G <= 1.05 * mmin && (!st || m.P < st->P)) st = &m;
+    ch.P = st->P;
+    ch.mode = RIMO_MODE_HOLOGRAPHIC;
+    ch.check_h = true;
+    ch.est_m_g = st->m_G;
+    ch.est_cost = st->cost;
+    return ch;
+}
+
+}  // namespace planner
+}  // namespace rimo

@@ -1,0 +1,88 @@
+"""C ABI exports and the host planner against the oracle planner (CPU only).
+
+rimo_plan_estimate runs the planner of Section 3.4 on the host without touching a
+GPU, so the product's planning decisions are compared here with the oracle's.
+"""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import plan as opl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "rimo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rimo_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(rimo_lib):
+    names = header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(rimo_lib, n), n
+
+
+def test_version_and_last_error_without_gpu(rimo_lib):
+    assert b"sm_103a" in rimo_lib.rimo_version()
+    assert isinstance(rimo_lib.rimo_last_error(), bytes)
+
+
+def _params(pkg, n, fov, **kw):
+    return pkg.default_params(n, n, fov, fov, **kw)
+
+
+def test_invalid_arguments_are_rejected(rimo_lib):
+    import paper_2605_26347_gb300 as pkg
+    uvw = synth.make_uvw(100, 60, 1.28e9, 3)
+    for bad in (dict(nx=100), dict(oversampling=3), dict(kb_support=6), dict(max_wsupport=11),
+                dict(w_norm_frac=0.0), dict(plan_fraction=2.0), dict(tile_size=48)):
+        p = _params(pkg, 256, math.radians(1.0))
+        for k, v in bad.items():
+            setattr(p, k, v)
+        with pytest.raises(pkg.RimoError) as e:
+            pkg.estimate(uvw, p)
+        assert e.value.status == 1
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=256, fov=1.0, m=20000, steps=60, seed=1001, bins=4),
+    dict(n=256, fov=1.0, m=20000, steps=60, seed=1001, bins=0),
+    dict(n=512, fov=2.5, m=60000, steps=28800, seed=77, bins=0, budget=0),
+    dict(n=1024, fov=2.5, m=200000, steps=28800, seed=1002, bins=0, budget=40 * 2**30),
+])
+def test_planner_matches_oracle(case):
+    import paper_2605_26347_gb300 as pkg
+    uvw = synth.make_uvw(case["m"], case["steps"], 1.28e9, case["seed"])
+    fov = math.radians(case["fov"])
+    kw = dict(n_wbins=case["bins"], mem_budget_bytes=case.get("budget", 0))
+    est = pkg.estimate(uvw, _params(pkg, case["n"], fov, **kw))
+    ref = opl.choose(uvw, opl.PlanParams(nx=case["n"], ny=case["n"], fov_x=fov, fov_y=fov,
+                                         n_wbins=case["bins"], mem_budget_bytes=kw["mem_budget_bytes"]))
+    assert est["P"] == ref["P"]
+    assert est["mode"] == ref["mode"]
+    assert est["p_star"] == ref["p_star"]
+    assert est["subset"] == ref["subset"]
+    m = {d["P"]: d for d in ref["models"]}[est["P"]]
+    assert abs(est["est_m_g"] - m["m_G"]) <= 1e-9 * m["m_G"]
+    assert abs(est["est_cost"] - m["cost"]) <= 1e-9 * m["cost"]
+    assert abs(est["wsclean_p"] - opl.wsclean_bound(uvw[:, 2], fov, fov)) < 1e-9 * est["wsclean_p"]
+
+
+def test_planner_budget_regimes_match_oracle():
+    # Fig. 2 regimes forced by the budget: stored G at P*, nearest feasible P, holographic
+    import paper_2605_26347_gb300 as pkg
+    uvw = synth.make_uvw(30000, 60, 1.28e9, 5)
+    fov = math.radians(1.0)
+    ref = opl.choose(uvw, opl.PlanParams(nx=256, ny=256, fov_x=fov, fov_y=fov))
+    mG = sorted(d["m_G"] for d in ref["models"])
+    for budget in (0, int(mG[len(mG) // 2]), int(mG[0] * 1.0001), 1000):
+        est = pkg.estimate(uvw, _params(pkg, 256, fov, mem_budget_bytes=budget))
+        r = opl.choose(uvw, opl.PlanParams(nx=256, ny=256, fov_x=fov, fov_y=fov, mem_budget_bytes=budget))
+        assert (est["P"], est["mode"]) == (r["P"], r["mode"]), budget
