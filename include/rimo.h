@@ -219,6 +219,33 @@ rimo_status rimo_build_holographic(rimo_plan_t plan, void* stream);
 /* PSF: out = Phi^dagger Phi delta, delta at pixel (ny/2, nx/2); unnormalised. */
 rimo_status rimo_psf(rimo_plan_t plan, rimo_cfloat* out_dev, void* stream);
 
+/*
+ * Stage timers (tracing).  When enabled, every kernel group the plan enqueues is
+ * bracketed by CUDA events recorded on the same stream.  Stages:
+ *   0 forward rows pass (Z_p and 2-D DFT along l)   1 forward cols pass
+ *   2 grid clear                                   3 de-grid / grid / fused G^dagger G
+ *   4 inverse cols pass                            5 inverse rows pass (Z_p^dagger, sum over p)
+ *   6 G build                                      7 H build
+ *   8 H apply                                      9 surrogate MLP (train / fused generation)
+ *   10..15 reserved
+ * rimo_profile_enable(plan, on) starts (on != 0) or stops recording; it does not reset.
+ * rimo_profile_read synchronises the pending events, adds their durations to the
+ * running totals and copies, for the first n stages, the total milliseconds (ms[n])
+ * and the number of kernel launches (launches[n]); reset != 0 clears the totals after
+ * copying.  Either output pointer may be NULL.  Errors: INVALID_ARG, CUDA.
+ */
+#define RIMO_N_STAGES 16
+rimo_status rimo_profile_enable(rimo_plan_t plan, int32_t on);
+rimo_status rimo_profile_read(rimo_plan_t plan, double* ms, int64_t* launches, int32_t n,
+                              int32_t reset);
+
+/*
+ * Device status of a plan: synchronises `stream`, then returns RIMO_ERR_TIMEOUT (and
+ * clears the flag) if a kernel of this plan gave up a bounded wait since the last call
+ * (its results are then invalid), else RIMO_OK.  Kernels never spin without a bound.
+ */
+rimo_status rimo_plan_status(rimo_plan_t plan, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rimo_last_error(void);
 

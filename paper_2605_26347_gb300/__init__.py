@@ -155,6 +155,17 @@ class Plan:
         _lib.check(self._lib.rimo_psf(self._h, out.data_ptr(), _stream_ptr(stream)))
         return out
 
+    def profile(self, on: bool = True):
+        """Start or stop the per-stage CUDA-event timers (rimo_profile_enable)."""
+        _lib.check(self._lib.rimo_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{stage: (total ms, kernel launches)} since the last reset (rimo_profile_read)."""
+        ms = (C.c_double * _lib.N_STAGES)()
+        ln = (C.c_int64 * _lib.N_STAGES)()
+        _lib.check(self._lib.rimo_profile_read(self._h, ms, ln, _lib.N_STAGES, int(reset)))
+        return {name: (ms[i], ln[i]) for i, name in enumerate(_lib.STAGE_NAMES)}
+
     def build_holographic(self, stream=None):
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 

@@ -12,6 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librimo.so")
 
 RIMO_OK = 0
+N_STAGES = 16
+STAGE_NAMES = ["fwd_rows", "fwd_cols", "grid_clear", "gtg", "inv_cols", "inv_rows", "g_build",
+               "h_build", "h_apply", "mlp"]
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "CUDA", 5: "TIMEOUT",
           6: "UNSUPPORTED", 7: "STATE"}
 MODE_AUTO, MODE_STORED_G, MODE_HOLOGRAPHIC, MODE_SURROGATE, MODE_ONTHEFLY = 0, 1, 2, 3, 4
@@ -82,6 +85,9 @@ _PROTOS = {
     "rimo_apply_phi_adj_phi": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "rimo_build_holographic": (C.c_int, [_P, _P]),
     "rimo_psf": (C.c_int, [_P, _P, _P]),
+    "rimo_plan_status": (C.c_int, [_P, _P]),
+    "rimo_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "rimo_profile_read": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

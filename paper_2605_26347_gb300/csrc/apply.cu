@@ -7,6 +7,51 @@
 
 namespace rimo {
 
+static cudaEvent_t prof_event(rimo_plan* p) {
+    if (!p->prof_pool.empty()) {
+        cudaEvent_t e = p->prof_pool.back();
+        p->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    RIMO_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void prof_begin(rimo_plan* p, int stage, cudaStream_t s) {
+    if (!p->prof_on) return;
+    p->prof_open_stage = stage;
+    p->prof_open_event = prof_event(p);
+    RIMO_CUDA(cudaEventRecord(p->prof_open_event, s));
+}
+
+void prof_end(rimo_plan* p, int launches, cudaStream_t s) {
+    if (!p->prof_on || p->prof_open_stage < 0) return;
+    cudaEvent_t b = prof_event(p);
+    RIMO_CUDA(cudaEventRecord(b, s));
+    p->prof_pending.push_back({p->prof_open_stage, launches, p->prof_open_event, b});
+    p->prof_open_stage = -1;
+    p->prof_open_event = nullptr;
+}
+
+static void prof_collect(rimo_plan* p) {
+    for (auto& m : p->prof_pending) {
+        RIMO_CUDA(cudaEventSynchronize(m.b));
+        float ms = 0.f;
+        RIMO_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
+        p->prof_ms[m.stage] += ms;
+        p->prof_launches[m.stage] += m.launches;
+        p->prof_pool.push_back(m.a);
+        p->prof_pool.push_back(m.b);
+    }
+    p->prof_pending.clear();
+}
+
+static int gtg_launches(const rimo_plan* p, int b, int mode) {
+    (void)mode;
+    return p->bins[b].t1 > p->bins[b].t0 ? 1 : 0;
+}
+
 static void check_plan(rimo_plan* p) {
     if (!p) fail(RIMO_ERR_INVALID_ARG, "null plan");
 }
@@ -17,23 +62,50 @@ static void zero_image(rimo_plan* p, rimo_cfloat* out, cudaStream_t s) {
     RIMO_CUDA(cudaMemsetAsync(out, 0, (size_t)p->nx * p->ny * sizeof(float2), s));
 }
 
+static void fwd(rimo_plan* p, int b, const float2* x, cudaStream_t s) {
+    prof_begin(p, ST_FWD_ROWS, s);
+    launch_fwd_rows(p, b, x, p->d_AB, s);
+    prof_end(p, 1, s);
+    prof_begin(p, ST_FWD_COLS, s);
+    launch_fwd_cols(p, p->d_AB, p->d_X, s);
+    prof_end(p, 1, s);
+}
+
+static void reset_schedulers(rimo_plan* p, cudaStream_t s) {
+    RIMO_CUDA(cudaMemsetAsync(p->d_counter, 0, (size_t)p->P * sizeof(int32_t), s));
+}
+
+static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cudaStream_t s) {
+    prof_begin(p, ST_INV_COLS, s);
+    launch_inv_cols(p, b, p->d_AB, s);
+    prof_end(p, 1, s);
+    prof_begin(p, ST_INV_ROWS, s);
+    launch_inv_rows(p, b, p->d_AB, out, first ? 0 : 1, real_only, s);
+    prof_end(p, 1, s);
+}
+
+static void gtg(rimo_plan* p, int b, int mode, const float2* y_in, float2* y_out, cudaStream_t s) {
+    prof_begin(p, ST_GTG, s);
+    launch_gtg(p, b, mode, y_in, y_out, s);
+    prof_end(p, gtg_launches(p, b, mode), s);
+}
+
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {
+    reset_schedulers(p, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
-        launch_fwd_rows(p, b, x, p->d_AB, s);
-        launch_fwd_cols(p, p->d_AB, p->d_X, s);
-        launch_gtg(p, b, 0, p->d_X, nullptr, nullptr, y, s);
+        fwd(p, b, x, s);
+        gtg(p, b, 0, nullptr, y, s);
     }
 }
 
 void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
     bool first = true;
+    reset_schedulers(p, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
-        RIMO_CUDA(cudaMemsetAsync(p->d_Xh, 0, (size_t)p->gx * p->gy * sizeof(float2), s));
-        launch_gtg(p, b, 1, nullptr, p->d_Xh, y, nullptr, s);
-        launch_inv_cols(p, p->d_Xh, p->d_AB, s);
-        launch_inv_rows(p, b, p->d_AB, x, first ? 0 : 1, 0, s);
+        gtg(p, b, 1, y, nullptr, s);
+        inv(p, b, x, first, 0, s);
         first = false;
     }
     if (first) zero_image(p, (rimo_cfloat*)x, s);
@@ -41,14 +113,12 @@ void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
 
 void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s) {
     bool first = true;
+    reset_schedulers(p, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
-        launch_fwd_rows(p, b, x, p->d_AB, s);
-        launch_fwd_cols(p, p->d_AB, p->d_X, s);
-        RIMO_CUDA(cudaMemsetAsync(p->d_Xh, 0, (size_t)p->gx * p->gy * sizeof(float2), s));
-        launch_gtg(p, b, 2, p->d_X, p->d_Xh, nullptr, nullptr, s);
-        launch_inv_cols(p, p->d_Xh, p->d_AB, s);
-        launch_inv_rows(p, b, p->d_AB, out, first ? 0 : 1, real_only, s);
+        fwd(p, b, x, s);
+        gtg(p, b, 2, nullptr, nullptr, s);
+        inv(p, b, out, first, real_only, s);
         first = false;
     }
     if (first) zero_image(p, (rimo_cfloat*)out, s);
@@ -108,6 +178,46 @@ rimo_status rimo_psf(rimo_plan_t p, rimo_cfloat* out, void* stream) {
     if (!out) fail(RIMO_ERR_INVALID_ARG, "null buffer");
     apply_phi_adj_phi(p, p->d_delta, (float2*)out, 0, (cudaStream_t)stream);
     RIMO_CUDA(cudaGetLastError());
+    RIMO_API_END
+}
+
+rimo_status rimo_profile_enable(rimo_plan_t p, int32_t on) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    p->prof_on = on != 0;
+    RIMO_API_END
+}
+
+rimo_status rimo_profile_read(rimo_plan_t p, double* ms, int64_t* launches, int32_t n,
+                              int32_t reset) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    if (n < 0 || n > RIMO_N_STAGES) fail(RIMO_ERR_INVALID_ARG, "n must be in [0, RIMO_N_STAGES]");
+    prof_collect(p);
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = p->prof_ms[i];
+        if (launches) launches[i] = p->prof_launches[i];
+    }
+    if (reset)
+        for (int i = 0; i < RIMO_N_STAGES; ++i) {
+            p->prof_ms[i] = 0.0;
+            p->prof_launches[i] = 0;
+        }
+    RIMO_API_END
+}
+
+rimo_status rimo_plan_status(rimo_plan_t p, void* stream) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t flag = 0;
+    RIMO_CUDA(cudaMemcpyAsync(&flag, p->d_status, sizeof(flag), cudaMemcpyDeviceToHost, s));
+    RIMO_CUDA(cudaStreamSynchronize(s));
+    if (flag != 0) {
+        RIMO_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s));
+        RIMO_CUDA(cudaStreamSynchronize(s));
+        fail(RIMO_ERR_TIMEOUT, "a bounded device wait ran out (code " + std::to_string(flag) + ")");
+    }
     RIMO_API_END
 }
 

@@ -291,24 +291,56 @@ __global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (102
     }
 }
 
+// The gridded grid of one bin, read as the sum of the accumulator patches of the active
+// uv-tiles that cover a cell (its own tile, and the halos of the tiles before it along u
+// and v); cells no active tile reaches are zero.
+struct PatchSrc {
+    const float2* patch;  // [slot][PW * PW]
+    const int* slot;      // [tu * ntv + tv] -> slot or -1
+    int ntu, ntv, shift, H, PW;
+};
+
+__device__ __forceinline__ float2 patch_at(const PatchSrc& P, int u, int v) {
+    const int TS = 1 << P.shift;
+    const int tu = u >> P.shift, au = u & (TS - 1), tv = v >> P.shift, av = v & (TS - 1);
+    const size_t np = (size_t)P.PW * P.PW;
+    float2 acc = make_float2(0.f, 0.f);
+    int s = __ldg(&P.slot[tu * P.ntv + tv]);
+    if (s >= 0) acc = __ldg(&P.patch[s * np + au * P.PW + av]);
+    const bool hu = au < P.H, hv = av < P.H;
+    const int tu1 = tu == 0 ? P.ntu - 1 : tu - 1, tv1 = tv == 0 ? P.ntv - 1 : tv - 1;
+    if (hu) {
+        s = __ldg(&P.slot[tu1 * P.ntv + tv]);
+        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av]));
+    }
+    if (hv) {
+        s = __ldg(&P.slot[tu * P.ntv + tv1]);
+        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + au * P.PW + av + TS]));
+    }
+    if (hu && hv) {
+        s = __ldg(&P.slot[tu1 * P.ntv + tv1]);
+        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av + TS]));
+    }
+    return acc;
+}
+
 // ----------------------------------------------------------------------------- inverse cols
 // grid: gx / RB blocks; rows u of Xh (2N cells along v) -> B[i][u] for the N image rows.
 template <int N, int RB>
-__global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B,
+__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 256 ? 2 : 1) inv_cols_kernel(PatchSrc src, float2* __restrict__ B,
                                                                 int gx, const float2* __restrict__ tw2N) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * (N + N / 16);
-    const size_t u = (size_t)blockIdx.x * RB + g;
-    const float2* in = Xh + u * (2 * N);
+    const int u = blockIdx.x * RB + g;
     float2 v[16];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + T * m;
-            float2 a = __ldg(&in[k]), b = __ldg(&in[k + N]);
+            float2 a = patch_at(src, u, k), b = patch_at(src, u, k + N);
             v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
         }
         fft_n<N, true>(v, sm, t, tw2N);
@@ -387,6 +419,10 @@ static ZArgs zargs(const rimo_plan* p, int bin) {
 
 template <int N>
 static constexpr int rows_per_block() { return (N / 16) >= 64 ? 4 : 256 / (N / 16); }
+// the inverse cols pass sums up to four patches per input point: fewer rows per block
+// leave it the registers to keep them in flight
+template <int N>
+static constexpr int inv_rows_per_block() { return (N / 16) >= 256 ? 2 : rows_per_block<N>(); }
 template <int N>
 static constexpr int groups_per_block() { return (N / 16) >= 256 ? 1 : 256 / (N / 16); }
 
@@ -428,11 +464,19 @@ static void fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream
 }
 
 template <int N>
-static void inv_cols(const rimo_plan* p, const float2* Xh, float2* B, cudaStream_t s) {
-    constexpr int RB = rows_per_block<N>();
+static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
+    constexpr int RB = inv_rows_per_block<N>();
     const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
     set_smem(inv_cols_kernel<N, RB>, sm);
-    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(Xh, B, p->gx, p->tab.tw_y);
+    PatchSrc src;
+    src.ntu = p->gx / p->TS;
+    src.ntv = p->gy / p->TS;
+    src.patch = p->d_patch;
+    src.slot = p->d_slot + (size_t)bin * src.ntu * src.ntv;
+    src.shift = p->TS == 64 ? 6 : 5;
+    src.H = p->H;
+    src.PW = p->PW;
+    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(src, B, p->gx, p->tab.tw_y);
 }
 
 template <int N>
@@ -451,8 +495,8 @@ void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, c
 void launch_fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s) {
     RIMO_DISPATCH_N(p->ny, fwd_cols<NN>(p, At, X, s));
 }
-void launch_inv_cols(const rimo_plan* p, const float2* Xh, float2* B, cudaStream_t s) {
-    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, Xh, B, s));
+void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, bin, B, s));
 }
 void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,
                      int real_only, cudaStream_t s) {

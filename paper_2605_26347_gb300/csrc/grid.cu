@@ -2,15 +2,25 @@
 // (G_p^dagger, Eq. 8) and the fused G_p^dagger G_p of Phi^dagger Phi.
 //
 // Layout.  Visibilities of a w-bin are sorted by the uv-tile (TS x TS grid cells)
-// holding their first grid cell.  One thread block owns one uv-tile: it stages the
-// (TS + H)^2 patch of the grid that the tile's visibilities can touch (H = largest
-// tile side - 1) in shared memory, one warp per visibility reads the visibility's
-// S x S taps once (coalesced), gathers the patch (de-gridding, warp-shuffle reduction)
-// and scatters conj(taps) * y into a privatised shared-memory accumulator.  The
-// accumulator is added to the global grid once per cell.  Patches of neighbouring
-// tiles overlap by H cells, so the gridding launches run the four tile colourings
-// (even/odd tile index along u and v) one after another; within a colouring no two
-// patches overlap and no global atomics are needed.
+// holding their first grid cell, and their taps are stored tile after tile, so the
+// taps of consecutive visibilities of a tile are one contiguous byte range.
+//
+// Kernel.  Persistent thread blocks (one per SM) take work units (a uv-tile, or a slice
+// of a heavy one) in snake order over a heaviest-first schedule.  For a unit, the block
+// stages the (TS + H)^2 grid patch its visibilities can reach (H = largest tile side - 1)
+// in shared memory while a producer warp streams the taps of 16 visibilities at a time
+// with bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) through a
+// 4-deep shared-memory ring.
+//   de-grid : one warp per visibility reads its S x S taps from shared memory (lanes = two
+//             rows of 16 columns), gathers the patch and reduces y_k with warp shuffles;
+//   grid    : the same warp adds conj(taps) y_k into the block's shared accumulator patch
+//             (shared-memory atomic adds: visibilities of different warps may overlap).
+// The finished accumulator patch is written once to the unit's slot of the patch buffer
+// (slices of a split tile are then added into its first slot); the inverse transform sums
+// the overlapping halos of neighbouring patches as it reads them, so the gridded grid is
+// never cleared, materialised or written with global atomics.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rimo {
@@ -21,121 +31,328 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-constexpr int MAX_TAPS_PER_LANE = 12;  // ceil(19 * 19 / 32)
-
-// e / S for e < 361, S <= 19 by multiply-shift with ceil(2^16 / S)
+// e / S for e < 400, S <= 19 by multiply-shift with ceil(2^16 / S)
 __device__ __forceinline__ int div_small(int e, int magic) { return (e * magic) >> 16; }
 
-template <int MODE>  // 0: de-grid (y_out), 1: grid (y_in), 2: fused G^dagger G
-__global__ void __launch_bounds__(256) gtg_kernel(const TileDesc* __restrict__ tiles,
-                                                  const VisMeta* __restrict__ meta,
-                                                  const float2* const* __restrict__ gblk,
-                                                  const float2* __restrict__ X, float2* __restrict__ Xh,
-                                                  const float2* __restrict__ y_in, float2* __restrict__ y_out,
-                                                  int gx, int gy, int TS, int PW) {
-    extern __shared__ float2 sm[];
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after 2^22 suspended polls (seconds); never spins forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk asynchronous copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr int GTG_CONSUMERS = 16;                        // consumer warps
+constexpr int GTG_THREADS = (GTG_CONSUMERS + 1) * 32;   // + one producer warp
+constexpr int GTG_NBUF = 4;   // maximum depth of the tap ring (the plan may use fewer)
+constexpr int GTG_CV = 16;    // visibilities per chunk (one per consumer warp when de-gridding)
+
+struct GtgArgs {
+    const TileDesc* units;  // this bin's work units, in patch-slot order
+    const int* sched;       // unit indices, heaviest first
+    const ChunkDesc* chunks;
+    int nunits;
+    const VisMeta* meta;
+    const float2* const* gblk;
+    const float2* X;        // forward grid [gx][gy]
+    float2* patch;          // accumulator patch per unit slot
+    const float2* y_in;
+    float2* y_out;
+    int gx, gy, TS, PW;
+    int chunk_bytes;
+    int nbuf;               // ring depth in use, 2..GTG_NBUF
+    int* status;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(GTG_CONSUMERS * 32) : "memory");
+}
+
+// unit processed by block c in round r: snake order over the heaviest-first schedule
+__device__ __forceinline__ int unit_of(int r, int c, int G) { return r * G + ((r & 1) ? (G - 1 - c) : c); }
+
+// One visibility by one warp, tile side S known at compile time.  Lane = (row parity,
+// column): half-warp h takes rows h, h + 2, ...; column c (and c + 16 when S > 16).
+// The taps stay in registers between the de-grid and the grid step.
+template <int S, int MODE>
+__device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const float2* __restrict__ Xs,
+                                         float2* As, int pbase, int PW, int lane, uint32_t orig,
+                                         const float2* __restrict__ y_in, float2* __restrict__ y_out) {
     constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
-    float2* Xs = sm;
-    float2* As = sm + (GATHER ? PW * PW : 0);
-    const TileDesc td = tiles[blockIdx.x];
-    const int u0 = td.tu * TS, v0 = td.tv * TS;
-    const int npatch = PW * PW;
-    for (int e = threadIdx.x; e < npatch; e += blockDim.x) {
-        const int a = e / PW, b = e - a * PW;
-        int gu = u0 + a, gv = v0 + b;
-        if (gu >= gx) gu -= gx;
-        if (gv >= gy) gv -= gy;
-        if (GATHER) Xs[e] = X[(size_t)gu * gy + gv];
-        if (SCATTER) As[e] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t k = td.vb + warp; k < td.ve; k += nw) {
-        const VisMeta mt = meta[k];
-        const int du = mt.pos & 255, dv = (mt.pos >> 8) & 255, S = (mt.pos >> 16) & 255;
-        const float2* T = gblk[mt.pos >> 24] + mt.off;
-        const int n = S * S;
-        const int magic = (65536 + S - 1) / S;
-        const int base = du * PW + dv;
-        float2 tv[MAX_TAPS_PER_LANE];
-        int sidx[MAX_TAPS_PER_LANE];
-        float ar = 0.f, ai = 0.f;
+    constexpr int NR = (S + 1) / 2, NC = (S + 15) / 16;
+    const int half = lane >> 4, col = lane & 15;
+    const float2* Tl = T + half * S + col;
+    const int xl = pbase + half * PW + col;
+    float2 t[NR][NC];
+    float ar = 0.f, ai = 0.f;
 #pragma unroll
-        for (int it = 0; it < MAX_TAPS_PER_LANE; ++it) {
-            const int e = lane + 32 * it;
-            if (e < n) {
-                const int a = div_small(e, magic), b = e - a * S;
-                tv[it] = __ldg(&T[e]);
-                sidx[it] = base + a * PW + b;
-                if (GATHER) {
-                    const float2 x = Xs[sidx[it]];
-                    ar = fmaf(tv[it].x, x.x, fmaf(-tv[it].y, x.y, ar));
-                    ai = fmaf(tv[it].x, x.y, fmaf(tv[it].y, x.x, ai));
-                }
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const bool ok = (2 * i + half < S) && (col + 16 * j < S);
+            t[i][j] = ok ? Tl[2 * i * S + 16 * j] : make_float2(0.f, 0.f);
+            if (GATHER && ok) {
+                const float2 x = Xs[xl + 2 * i * PW + 16 * j];
+                ar = fmaf(t[i][j].x, x.x, fmaf(-t[i][j].y, x.y, ar));
+                ai = fmaf(t[i][j].x, x.y, fmaf(t[i][j].y, x.x, ai));
             }
         }
-        float2 y;
-        if (GATHER) {
-            y.x = warp_sum(ar);
-            y.y = warp_sum(ai);
-            if (MODE == 0 && lane == 0) y_out[mt.orig] = y;
-        } else {
-            y = __ldg(&y_in[mt.orig]);
-        }
-        if (SCATTER) {
-#pragma unroll
-            for (int it = 0; it < MAX_TAPS_PER_LANE; ++it) {
-                const int e = lane + 32 * it;
-                if (e < n) {
-                    // conj(t) * y
-                    atomicAdd(&As[sidx[it]].x, fmaf(tv[it].x, y.x, tv[it].y * y.y));
-                    atomicAdd(&As[sidx[it]].y, fmaf(tv[it].x, y.y, -tv[it].y * y.x));
-                }
-            }
-        }
+    float2 y;
+    if (GATHER) {
+        y.x = warp_sum(ar);
+        y.y = warp_sum(ai);
+        if (MODE == 0 && lane == 0) y_out[orig] = y;
+    } else {
+        y = y_in[orig];
     }
     if (SCATTER) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < npatch; e += blockDim.x) {
-            const float2 acc = As[e];
-            if (acc.x == 0.f && acc.y == 0.f) continue;
-            const int a = e / PW, b = e - a * PW;
-            int gu = u0 + a, gv = v0 + b;
-            if (gu >= gx) gu -= gx;
-            if (gv >= gy) gv -= gy;
-            float2* dst = &Xh[(size_t)gu * gy + gv];
-            const float2 o = *dst;
-            *dst = make_float2(o.x + acc.x, o.y + acc.y);
-        }
+#pragma unroll
+        for (int i = 0; i < NR; ++i)
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const bool ok = (2 * i + half < S) && (col + 16 * j < S);
+                if (ok) {
+                    float* a = reinterpret_cast<float*>(&As[xl + 2 * i * PW + 16 * j]);
+                    atomicAdd(a, fmaf(t[i][j].x, y.x, t[i][j].y * y.y));  // conj(t) y
+                    atomicAdd(a + 1, fmaf(t[i][j].x, y.y, -t[i][j].y * y.x));
+                }
+            }
     }
 }
 
 template <int MODE>
-static void gtg_launch(const rimo_plan* p, int t0, int t1, const float2* X, float2* Xh,
-                       const float2* y_in, float2* y_out, cudaStream_t s) {
-    if (t1 <= t0) return;
-    const size_t sm = (size_t)p->PW * p->PW * sizeof(float2) * (MODE == 2 ? 2 : 1);
-    static bool done = false;
-    if (!done) {
-        RIMO_CUDA(cudaFuncSetAttribute(gtg_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       2 * 96 * 96 * (int)sizeof(float2)));
-        done = true;
+__device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float2* Xs, float2* As, int pbase,
+                                             int PW, int lane, uint32_t orig, const float2* y_in,
+                                             float2* y_out) {
+    switch (S) {
+        case 3: vis_tile<3, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 5: vis_tile<5, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 7: vis_tile<7, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 9: vis_tile<9, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 11: vis_tile<11, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 13: vis_tile<13, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 15: vis_tile<15, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 17: vis_tile<17, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        default: vis_tile<19, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
     }
-    gtg_kernel<MODE><<<t1 - t0, 256, sm, s>>>(p->d_tiles + t0, p->d_meta, p->d_gblock_ptrs, X, Xh, y_in,
-                                              y_out, p->gx, p->gy, p->TS, p->PW);
 }
 
-void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* X, float2* Xh,
-                const float2* y_in, float2* y_out, cudaStream_t s) {
-    const auto& br = p->bins[bin];
-    if (mode == 0) {  // read-only on the grid: all colourings in one launch
-        gtg_launch<0>(p, br.tile_off[0], br.tile_off[4], X, Xh, y_in, y_out, s);
+// Warp-specialised pipeline per block:
+//   producer warp : for each chunk (16 consecutive visibilities of a unit) streams their
+//                   16-byte metadata and their taps (one contiguous range, from a chunk
+//                   descriptor) into ring slot b with cp.async.bulk, once the consumers
+//                   released the slot;
+//   consumer warps: wait full[b]; each takes one visibility of the chunk, de-grids it
+//                   and grids conj(taps) y_k into the block's shared accumulator patch
+//                   (shared-memory atomic adds: visibilities of different warps may
+//                   overlap); then arrive on empty[b].
+// Only unit boundaries (patch load / store) synchronise all consumers.
+template <int MODE>  // 0: de-grid (y_out), 1: grid (y_in), 2: fused de-grid + grid
+__global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
+    constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+    uint64_t* empty = full + GTG_NBUF;
+    VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + 128);          // GTG_NBUF x 16 entries
+    float2* taps = reinterpret_cast<float2*>(smraw + 128 + GTG_NBUF * GTG_CV * sizeof(VisMeta));
+    const int PW = A.PW, npatch = PW * PW;
+    const int chunk_f2 = A.chunk_bytes / 8;
+    const uint32_t NB = (uint32_t)A.nbuf;
+    float2* Xs = taps + (size_t)NB * chunk_f2;
+    float2* As = Xs + (GATHER ? npatch : 0);
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, cb = blockIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < GTG_NBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], GTG_CONSUMERS);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == GTG_CONSUMERS) {
+        // ------------------------------------------------------------ producer
+        if (lane != 0) return;
+        uint32_t g = 0;
+        for (int r = 0;; ++r) {
+            const int idx = unit_of(r, cb, G);
+            if (idx >= A.nunits) break;
+            const TileDesc td = A.units[A.sched[idx]];
+            const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
+            for (int c = 0; c < nchunks; ++c, ++g) {
+                const ChunkDesc cd = A.chunks[td.cb + c];
+                const int64_t v0 = td.vb + (int64_t)c * GTG_CV;
+                const uint32_t nv = (uint32_t)((td.ve - v0) < GTG_CV ? (td.ve - v0) : GTG_CV);
+                const uint32_t b = g % NB, use = g / NB;
+                if (use > 0 && !s_abort && !mbar_wait_bounded(&empty[b], (use - 1) & 1)) {
+                    s_abort = 1;
+                    atomicExch(A.status, 1);
+                }
+                if (s_abort) {
+                    // let the copies already in flight land before the block may exit
+                    for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
+                        (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
+                    return;
+                }
+                mbar_arrive_expect_tx(&full[b], cd.bytes + nv * (uint32_t)sizeof(VisMeta));
+                bulk_g2s(mring + b * GTG_CV, A.meta + v0, nv * (uint32_t)sizeof(VisMeta), &full[b]);
+                bulk_g2s(taps + (size_t)b * chunk_f2, A.gblk[cd.block] + cd.off, cd.bytes, &full[b]);
+            }
+        }
         return;
     }
-    for (int ph = 0; ph < 4; ++ph) {
-        if (mode == 1) gtg_launch<1>(p, br.tile_off[ph], br.tile_off[ph + 1], X, Xh, y_in, y_out, s);
-        else gtg_launch<2>(p, br.tile_off[ph], br.tile_off[ph + 1], X, Xh, y_in, y_out, s);
+
+    // ---------------------------------------------------------------- consumers
+    uint32_t g = 0;
+    for (int r = 0;; ++r) {
+        const int idx = unit_of(r, cb, G);
+        if (idx >= A.nunits) break;
+        const int slot = A.sched[idx];
+        const TileDesc td = A.units[slot];
+        const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
+        const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
+        for (int a = warp; a < PW; a += GTG_CONSUMERS) {
+            int gu = u0 + a;
+            if (gu >= A.gx) gu -= A.gx;
+            for (int b = lane; b < PW; b += 32) {
+                if (GATHER) {
+                    int gv = v0 + b;
+                    if (gv >= A.gy) gv -= A.gy;
+                    Xs[a * PW + b] = A.X[(size_t)gu * A.gy + gv];
+                }
+                if (SCATTER) As[a * PW + b] = make_float2(0.f, 0.f);
+            }
+        }
+        consumers_sync();
+        for (int c = 0; c < nchunks; ++c, ++g) {
+            const uint32_t b = g % NB, par = (g / NB) & 1;
+            if (!s_abort && !mbar_wait_bounded(&full[b], par)) {
+                s_abort = 1;
+                atomicExch(A.status, 1);
+            }
+            const int64_t cv0 = td.vb + (int64_t)c * GTG_CV;
+            const int ncv = (int)((td.ve - cv0) < GTG_CV ? (td.ve - cv0) : GTG_CV);
+            if (!s_abort && warp < ncv) {
+                const VisMeta mt = mring[b * GTG_CV + warp];
+                const int du = mt.pos & 255, dv = (mt.pos >> 8) & 255, S = (mt.pos >> 16) & 255;
+                const int loc = (int)(mt.off - mring[b * GTG_CV].off);
+                vis_dispatch<MODE>(S, taps + (size_t)b * chunk_f2 + loc, Xs, As, du * PW + dv, PW, lane,
+                                   mt.orig, A.y_in, A.y_out);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+        }
+        consumers_sync();
+        if (SCATTER && !s_abort) {
+            float2* dst = A.patch + (size_t)slot * npatch;
+            for (int e = tid; e < npatch; e += GTG_CONSUMERS * 32) dst[e] = As[e];
+        }
+        consumers_sync();
     }
+}
+
+// Adds the patches of the extra units of each split tile into its first unit's slot.
+__global__ void __launch_bounds__(256) merge_patches_kernel(float2* __restrict__ patch,
+                                                            const int2* __restrict__ groups, int npatch) {
+    const int2 gr = groups[blockIdx.x];
+    float2* dst = patch + (size_t)gr.x * npatch;
+    for (int e = threadIdx.x; e < npatch; e += blockDim.x) {
+        float2 acc = dst[e];
+        for (int q = 1; q < gr.y; ++q) {
+            const float2 v = patch[(size_t)(gr.x + q) * npatch + e];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        dst[e] = acc;
+    }
+}
+
+size_t gtg_smem(const rimo_plan* p, int mode, int nbuf) {
+    const size_t npatch = (size_t)p->PW * p->PW * sizeof(float2);
+    return 128 + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * p->chunk_bytes +
+           (mode == 2 ? 2 : 1) * npatch;
+}
+
+template <int MODE>
+static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_out, cudaStream_t s) {
+    const auto& br = p->bins[bin];
+    const int nu = br.t1 - br.t0;
+    if (nu <= 0) return;
+    GtgArgs A;
+    A.units = p->d_tiles + br.t0;
+    A.sched = p->d_sched + br.t0;
+    A.chunks = p->d_chunks;
+    A.nunits = nu;
+    A.meta = p->d_meta;
+    A.gblk = p->d_gblock_ptrs;
+    A.X = p->d_X;
+    A.patch = p->d_patch;
+    A.y_in = y_in;
+    A.y_out = y_out;
+    A.gx = p->gx;
+    A.gy = p->gy;
+    A.TS = p->TS;
+    A.PW = p->PW;
+    A.chunk_bytes = p->chunk_bytes;
+    A.status = p->d_status;
+    const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
+    A.nbuf = GTG_NBUF;
+    while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf) > limit) --A.nbuf;
+    const size_t sm = gtg_smem(p, MODE, A.nbuf);
+    if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
+    RIMO_CUDA(cudaFuncSetAttribute(gtg_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int grid = std::min(nu, p->n_sm);
+    gtg_kernel<MODE><<<grid, GTG_THREADS, sm, s>>>(A);
+    if (MODE != 0 && br.m1 > br.m0)
+        merge_patches_kernel<<<br.m1 - br.m0, 256, 0, s>>>(p->d_patch, p->d_merge + br.m0, p->PW * p->PW);
+}
+
+void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,
+                cudaStream_t s) {
+    if (mode == 0) gtg_run<0>(p, bin, y_in, y_out, s);
+    else if (mode == 1) gtg_run<1>(p, bin, y_in, y_out, s);
+    else gtg_run<2>(p, bin, y_in, y_out, s);
 }
 
 // ---------------------------------------------------------------------------

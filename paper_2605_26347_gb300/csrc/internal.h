@@ -40,11 +40,22 @@ static_assert(sizeof(VisMeta) == 16, "VisMeta must stay 16 bytes");
 struct TileDesc {
     int32_t tu, tv;
     int64_t vb, ve;
+    int64_t cb;   // index of the unit's first chunk descriptor
 };
+
+// One chunk of at most 16 consecutive visibilities of a unit: their taps are the byte
+// range [8 off, 8 off + bytes) of Fourier block `block`.
+struct ChunkDesc {
+    int64_t off;
+    uint32_t bytes;
+    uint32_t block;
+};
+static_assert(sizeof(ChunkDesc) == 16, "ChunkDesc must stay 16 bytes");
 
 struct BinRange {
     int64_t vb = 0, ve = 0;       // visibilities of the bin in sorted order
-    int32_t tile_off[5] = {0, 0, 0, 0, 0};  // tiles of phase q: [tile_off[q], tile_off[q+1])
+    int32_t t0 = 0, t1 = 0;       // work units of the bin: tiles_host[t0 .. t1) (patch slots 0 ..)
+    int32_t m0 = 0, m1 = 0;       // merge groups (split tiles) of the bin: merge_host[m0 .. m1)
     float w_hi = 0.f, w_lo = 0.f; // w_stack as a float pair (double-float)
     double w = 0.0;
 };
@@ -79,39 +90,66 @@ struct rimo_plan {
     std::vector<int32_t> bins_user, sw_user;
     std::vector<int32_t> inv_perm;               // caller index -> sorted position
     std::vector<rimo::BinRange> bins;
-    std::vector<rimo::TileDesc> tiles_host;      // all bins, grouped by (bin, phase)
+    std::vector<rimo::TileDesc> tiles_host;      // work units (uv-tiles or parts), grouped by bin
+    std::vector<int32_t> sched_host;             // per bin: unit indices, heaviest first
+    std::vector<int2> merge_host;                // per bin: (first slot, units) of split tiles
     std::vector<int64_t> block_bytes;
     bool holographic = false;
 
     // device
     rimo::VisMeta* d_meta = nullptr;
     rimo::TileDesc* d_tiles = nullptr;
+    int32_t* d_sched = nullptr;
+    rimo::ChunkDesc* d_chunks = nullptr;
+    int2* d_merge = nullptr;
     std::vector<float2*> d_gblocks;
     float2** d_gblock_ptrs = nullptr;
     float* d_wr = nullptr;     // residual w per visibility (sorted order)
     float* d_phiu = nullptr;   // fractional offsets (sorted order)
     float* d_phiv = nullptr;
     float2* d_X = nullptr;     // forward grid   (gx rows u, gy cols v)
-    float2* d_Xh = nullptr;    // gridded grid
+    float2* d_patch = nullptr; // gridded accumulator patch of every active tile of one bin
+    int32_t* d_slot = nullptr; // [bin][tu][tv] -> index of the tile's patch in d_patch, or -1
+    int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)
+    int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
+    int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     float2* d_AB = nullptr;    // half-transformed intermediates (2 nx ny)
     float2* d_delta = nullptr; // delta image for the PSF
     rimo::DevTables tab;
     std::vector<void*> owned;  // every cudaMalloc of the plan
+
+    // stage timers
+    bool prof_on = false;
+    struct Mark { int stage; int launches; cudaEvent_t a, b; };
+    std::vector<Mark> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[RIMO_N_STAGES] = {0};
+    int64_t prof_launches[RIMO_N_STAGES] = {0};
+    int prof_open_stage = -1;
+    cudaEvent_t prof_open_event = nullptr;
 };
 
 namespace rimo {
 
 void* dev_alloc(rimo_plan* p, size_t bytes);
 
+enum Stage { ST_FWD_ROWS = 0, ST_FWD_COLS = 1, ST_CLEAR = 2, ST_GTG = 3, ST_INV_COLS = 4,
+             ST_INV_ROWS = 5, ST_GBUILD = 6, ST_HBUILD = 7, ST_HAPPLY = 8, ST_MLP = 9 };
+// Bracket a group of `launches` kernel launches of one stage on stream s (no-op when off).
+void prof_begin(rimo_plan* p, int stage, cudaStream_t s);
+void prof_end(rimo_plan* p, int launches, cudaStream_t s);
+
 // Kernel launchers (defined in the .cu files).
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s);
 void launch_fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s);
-void launch_inv_cols(const rimo_plan* p, const float2* Xh, float2* B, cudaStream_t s);
+// reads the gridded grid of bin `bin` as the sum of the overlapping tile patches
+void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s);
 void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,
                      int real_only, cudaStream_t s);
-// mode 0: degrid (y_out), 1: grid (y_in), 2: fused degrid + grid
-void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* X, float2* Xh,
-                const float2* y_in, float2* y_out, cudaStream_t s);
+// mode 0: degrid (y_out), 1: grid (y_in), 2: fused degrid + grid.  Modes 1 and 2 write the
+// accumulator patch of every active tile of the bin to p->d_patch.
+void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,
+                cudaStream_t s);
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
 
 }  // namespace rimo

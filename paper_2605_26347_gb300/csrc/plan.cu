@@ -381,22 +381,49 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         p->bins[b].w_lo = (float)(p->w_stack[b] - (double)p->bins[b].w_hi);
     }
     if (p->block_bytes.size() > 255) fail(RIMO_ERR_INVALID_ARG, "more than 255 Fourier blocks");
-    // tile lists per (bin, phase), heaviest first for load balance
+    // work units: active uv-tiles, split into units of at most `cap` visibilities so that
+    // no unit outweighs a fraction of one SM's share of the bin; slots group the units of
+    // a tile contiguously (merge groups), the schedule orders units heaviest first
     p->tiles_host.clear();
+    p->sched_host.clear();
+    p->merge_host.clear();
     int n_active = 0;
+    std::vector<int32_t> slot((size_t)P * ntile, -1);
+    int nsm_host = 0;
+    {
+        int dev = 0;
+        RIMO_CUDA(cudaGetDevice(&dev));
+        RIMO_CUDA(cudaDeviceGetAttribute(&nsm_host, cudaDevAttrMultiProcessorCount, dev));
+    }
     for (int b = 0; b < P; ++b) {
-        for (int ph = 0; ph < 4; ++ph) {
-            p->bins[b].tile_off[ph] = (int32_t)p->tiles_host.size();
-            std::vector<const T*> sel;
-            for (const auto& x : tl[b])
-                if (((x.tu & 1) * 2 + (x.tv & 1)) == ph) sel.push_back(&x);
-            std::stable_sort(sel.begin(), sel.end(), [](const T* a, const T* c) {
-                return (a->ve - a->vb) > (c->ve - c->vb);
-            });
-            for (const T* x : sel) p->tiles_host.push_back(TileDesc{x->tu, x->tv, x->vb, x->ve});
+        const int64_t bin_vis = bstart[b + 1] - bstart[b];
+        const int64_t cap = std::max<int64_t>(256, (bin_vis + 2 * nsm_host - 1) / (2 * (int64_t)nsm_host));
+        p->bins[b].t0 = (int32_t)p->tiles_host.size();
+        p->bins[b].m0 = (int32_t)p->merge_host.size();
+        for (const auto& x : tl[b]) {
+            const int32_t first = (int32_t)p->tiles_host.size() - p->bins[b].t0;
+            const int64_t n = x.ve - x.vb;
+            const int64_t k = (n + cap - 1) / cap;
+            for (int64_t q = 0; q < k; ++q) {
+                const int64_t a = x.vb + n * q / k, e = x.vb + n * (q + 1) / k;
+                p->tiles_host.push_back(TileDesc{x.tu, x.tv, a, e, 0});
+            }
+            slot[(size_t)b * ntile + (size_t)x.tu * ntv + x.tv] = first;
+            if (k > 1) p->merge_host.push_back(make_int2(first, (int)k));
         }
-        p->bins[b].tile_off[4] = (int32_t)p->tiles_host.size();
+        p->bins[b].t1 = (int32_t)p->tiles_host.size();
+        p->bins[b].m1 = (int32_t)p->merge_host.size();
+        const int nu = p->bins[b].t1 - p->bins[b].t0;
+        std::vector<int32_t> ord(nu);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t i, int32_t j) {
+            const auto& A = p->tiles_host[p->bins[b].t0 + i];
+            const auto& B = p->tiles_host[p->bins[b].t0 + j];
+            return (A.ve - A.vb) > (B.ve - B.vb);
+        });
+        p->sched_host.insert(p->sched_host.end(), ord.begin(), ord.end());
         n_active += (int)tl[b].size();
+        p->max_tiles_bin = std::max(p->max_tiles_bin, nu);
     }
 
     // ---- caller-order host copies
@@ -408,7 +435,25 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     // ---- device
     build_tables(p, s);
     p->d_meta = upload(p, meta, s);
+    // chunk descriptors: 16 consecutive visibilities of a unit share one tap range
+    {
+        std::vector<ChunkDesc> ch;
+        for (auto& u : p->tiles_host) {
+            u.cb = (int64_t)ch.size();
+            for (int64_t v0 = u.vb; v0 < u.ve; v0 += 16) {
+                const int64_t v1 = std::min(u.ve, v0 + 16);
+                const VisMeta& m0 = meta[v0];
+                const VisMeta& m1 = meta[v1 - 1];
+                const int64_t S1 = (m1.pos >> 16) & 255;
+                const int64_t end = m1.off + S1 * S1 + ((S1 * S1) & 1);
+                ch.push_back(ChunkDesc{m0.off, (uint32_t)((end - m0.off) * 8), m0.pos >> 24});
+            }
+        }
+        p->d_chunks = upload(p, ch, s);
+    }
     p->d_tiles = upload(p, p->tiles_host, s);
+    p->d_sched = upload(p, p->sched_host, s);
+    p->d_merge = upload(p, p->merge_host, s);
     p->d_wr = upload(p, wr_s, s);
     p->d_phiu = upload(p, pu_s, s);
     p->d_phiv = upload(p, pv_s, s);
@@ -421,7 +466,19 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->d_gblock_ptrs = upload(p, ptrs, s);
     const size_t grid_elems = (size_t)gx * gy;
     p->d_X = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
-    p->d_Xh = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
+    p->d_slot = upload(p, slot, s);
+    p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
+    p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
+    p->d_status = (int32_t*)dev_alloc(p, sizeof(int32_t));
+    RIMO_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s));
+    {
+        int dev = 0;
+        RIMO_CUDA(cudaGetDevice(&dev));
+        RIMO_CUDA(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
+        const int s2 = p->max_S * p->max_S;
+        p->chunk_vis = 16;
+        p->chunk_bytes = p->chunk_vis * (s2 + (s2 & 1)) * (int)sizeof(float2);
+    }
     p->d_AB = (float2*)dev_alloc(p, (size_t)2 * p->nx * p->ny * sizeof(float2));
     p->d_delta = (float2*)dev_alloc(p, (size_t)p->nx * p->ny * sizeof(float2));
     RIMO_CUDA(cudaMemsetAsync(p->d_delta, 0, (size_t)p->nx * p->ny * sizeof(float2), s));
@@ -430,12 +487,15 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
                               sizeof(float2), cudaMemcpyHostToDevice, s));
     p->info.K = K;
     p->info.g_bytes = gbytes + (int64_t)M * (int64_t)sizeof(VisMeta);
-    p->info.scratch_bytes = (int64_t)(2 * grid_elems + 3 * (size_t)p->nx * p->ny) * 8;
+    p->info.scratch_bytes = (int64_t)(grid_elems + 3 * (size_t)p->nx * p->ny +
+                                      (size_t)p->max_tiles_bin * p->PW * p->PW) * 8;
     p->info.n_blocks = (int32_t)p->block_bytes.size();
     p->info.n_tiles = n_active;
 
     // ---- stage 3: precompute G on the device
+    prof_begin(p, ST_GBUILD, s);
     launch_gbuild(p, s);
+    prof_end(p, 1, s);
     RIMO_CUDA(cudaGetLastError());
     RIMO_CUDA(cudaStreamSynchronize(s));
 }
@@ -507,6 +567,12 @@ rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_param
 rimo_status rimo_plan_destroy(rimo_plan_t p) {
     if (!p) return RIMO_OK;
     for (void* ptr : p->owned) cudaFree(ptr);
+    for (auto& m : p->prof_pending) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+    if (p->prof_open_event) cudaEventDestroy(p->prof_open_event);
     delete p;
     return RIMO_OK;
 }
@@ -547,8 +613,8 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
             // the tile containing sorted position i
             int b = p->bins_user[idx[q]];
             int tu = -1, tv = -1;
-            for (int t = p->bins[b].tile_off[0]; t < p->bins[b].tile_off[4]; ++t)
-                if (p->tiles_host[t].vb <= i && i < p->tiles_host[t].ve) {
+            for (int t = p->bins[b].t0; t < p->bins[b].t1; ++t)
+                if (p->tiles_host[t].vb <= i && i < p->tiles_host[t].ve) {  // the unit holding i
                     tu = p->tiles_host[t].tu;
                     tv = p->tiles_host[t].tv;
                 }

@@ -66,6 +66,14 @@ def test_mono256_phi_adj_phi_and_real_part(mono256):
     assert rel(out_re.real, ref.real) < TOL
 
 
+def test_device_status_is_clean_after_applies(mono256):
+    import torch
+    import paper_2605_26347_gb300 as pkg
+    w, plan, _ = mono256
+    plan.phi_adj_phi(to_dev(w.sky))
+    pkg._lib.check(plan._lib.rimo_plan_status(plan._h, torch.cuda.current_stream().cuda_stream))
+
+
 def test_mono256_psf(mono256):
     _, plan, op = mono256
     psf = to_host(plan.psf())
