@@ -67,7 +67,7 @@ static void fwd(rimo_plan* p, int b, const float2* x, cudaStream_t s) {
     launch_fwd_rows(p, b, x, p->d_AB, s);
     prof_end(p, 1, s);
     prof_begin(p, ST_FWD_COLS, s);
-    launch_fwd_cols(p, p->d_AB, p->d_X, s);
+    launch_fwd_cols(p, b, p->d_AB, p->d_X, s);
     prof_end(p, 1, s);
 }
 

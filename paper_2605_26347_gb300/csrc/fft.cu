@@ -123,9 +123,11 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
 // One Stockham stage of radix R after NS points have been combined (NS * R <= N).
 // Thread t owns butterflies j = t + q T (q < 16/R, T = N/16); butterfly j reads
-// a[j + r N/R] and writes a'[(j / NS) NS R + j % NS + r NS].
+// a[j + r N/R] and writes a'[(j / NS) NS R + j % NS + r NS].  Its twiddles
+// W_{NS R}^{r (j mod NS)} come from the stage table tws[r NS + j mod NS], laid out so that
+// consecutive threads read consecutive entries.
 template <int N, int R, int NS, bool INV, bool FIRST, bool LAST>
-__device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tw2N) {
+__device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     constexpr int Q = 16 / R;
     if (!FIRST) {
@@ -141,8 +143,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
             const int jm = (t + q * T) & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const int e = r * jm * (N / (NS * R));
-                float2 w = __ldg(&tw2N[2 * e]);
+                float2 w = __ldg(&tws[r * NS + jm]);
                 v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
             }
         }
@@ -169,16 +170,18 @@ struct Plan16 {
 
 // In: v[m] = element t + T m of the input.  Out: element t + T m of the output is
 // v[out_slot<N>(m)].  All threads of the block must call it (block-wide barriers).
+// tws: the stage twiddle tables of length N (see stage_twiddles on the host): the second
+// stage's W_{16 R}^{r j} at [0, 16 R), the third stage's W_{256 R}^{r j} at [256, 256 + 256 R).
 template <int N, bool INV>
-__device__ __forceinline__ void fft_n(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tw2N) {
+__device__ __forceinline__ void fft_n(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tws) {
     constexpr int RL = Plan16<N>::R_LAST;
     if constexpr (N == 64 || N == 128 || N == 256) {
-        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tw2N);
-        fft_stage<N, RL, 16, INV, false, true>(v, sm, t, tw2N);
+        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, RL, 16, INV, false, true>(v, sm, t, tws);
     } else {
-        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tw2N);
-        fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tw2N);
-        fft_stage<N, RL, 256, INV, false, true>(v, sm, t, tw2N);
+        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tws);
+        fft_stage<N, RL, 256, INV, false, true>(v, sm, t, tws + 256);
     }
 }
 
@@ -226,7 +229,8 @@ __device__ __forceinline__ float2 z_factor(const ZArgs& z, int i, int j, int ic,
 // grid: ny / RB blocks of RB * N/16 threads; block b transforms image rows [b RB, b RB + RB).
 template <int N, int RB>
 __global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At,
-                                                                int ny, ZArgs z, const float2* __restrict__ tw2N) {
+                                                                int ny, ZArgs z, const float2* __restrict__ tw2N,
+                                                                const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (102
             if (r) val = cmul(val, __ldg(&tw2N[jc & (2 * N - 1)]));
             v[m] = val;
         }
-        fft_n<N, false>(v, sm, t, tw2N);
+        fft_n<N, false>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
         __syncthreads();
@@ -264,16 +268,27 @@ __global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (102
 
 // ----------------------------------------------------------------------------- forward cols
 // grid: rows / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
+// need[tu * ntv + tv] != 0 marks the tiles of X some active patch reads; the rest of X is
+// never read and not stored.  The RG rows of a block lie in one tile row.
 template <int N, int RG>
-__global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (1024 / (RG * N / 16)) : 1) fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X,
-                                                                const float2* __restrict__ tw2N) {
+__global__ void __launch_bounds__(RG * N / 16, (768 / (RG * N / 16)) > 0 ? (768 / (RG * N / 16)) : 1) fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X,
+                                                                const uint8_t* __restrict__ need, int shift,
+                                                                const float2* __restrict__ tw2N,
+                                                                const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RG * (N + N / 16));
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * (N + N / 16);
     const size_t u = (size_t)blockIdx.x * RG + g;
     const float2* in = At + u * N;
     float2* out = X + u * (2 * N);
+    {
+        const int ntv = (2 * N) >> shift;
+        const uint8_t* nr = need + (size_t)(((size_t)blockIdx.x * RG) >> shift) * ntv;
+        for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = nr[e];
+    }
+    __syncthreads();
     float2 v[16];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
@@ -285,9 +300,12 @@ __global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (102
             if (r) val = cmul(val, __ldg(&tw2N[ic & (2 * N - 1)]));
             v[m] = val;
         }
-        fft_n<N, false>(v, sm, t, tw2N);
+        fft_n<N, false>(v, sm, t, tws);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) out[2 * (t + T * m) + r] = v[out_slot<N>(m)];
+        for (int m = 0; m < 16; ++m) {
+            const int vv = 2 * (t + T * m) + r;
+            if (s_need[vv >> shift]) out[vv] = v[out_slot<N>(m)];
+        }
     }
 }
 
@@ -300,50 +318,68 @@ struct PatchSrc {
     int ntu, ntv, shift, H, PW;
 };
 
-__device__ __forceinline__ float2 patch_at(const PatchSrc& P, int u, int v) {
+// Fold one cell of row u (tile row tu, offset au) from the patches; s_own / s_up are the
+// slots of tile rows tu and tu - 1, cached in shared memory.
+__device__ __forceinline__ float2 fold_cell(const PatchSrc& P, const int* s_own, const int* s_up, int au,
+                                           bool hu, int v) {
     const int TS = 1 << P.shift;
-    const int tu = u >> P.shift, au = u & (TS - 1), tv = v >> P.shift, av = v & (TS - 1);
+    const int tv = v >> P.shift, av = v & (TS - 1);
     const size_t np = (size_t)P.PW * P.PW;
+    const int tv1 = tv == 0 ? P.ntv - 1 : tv - 1;
+    const bool hv = av < P.H;
     float2 acc = make_float2(0.f, 0.f);
-    int s = __ldg(&P.slot[tu * P.ntv + tv]);
+    int s = s_own[tv];
     if (s >= 0) acc = __ldg(&P.patch[s * np + au * P.PW + av]);
-    const bool hu = au < P.H, hv = av < P.H;
-    const int tu1 = tu == 0 ? P.ntu - 1 : tu - 1, tv1 = tv == 0 ? P.ntv - 1 : tv - 1;
-    if (hu) {
-        s = __ldg(&P.slot[tu1 * P.ntv + tv]);
-        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av]));
-    }
     if (hv) {
-        s = __ldg(&P.slot[tu * P.ntv + tv1]);
+        s = s_own[tv1];
         if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + au * P.PW + av + TS]));
     }
-    if (hu && hv) {
-        s = __ldg(&P.slot[tu1 * P.ntv + tv1]);
-        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av + TS]));
+    if (hu) {
+        s = s_up[tv];
+        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av]));
+        if (hv) {
+            s = s_up[tv1];
+            if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av + TS]));
+        }
     }
     return acc;
 }
 
 // ----------------------------------------------------------------------------- inverse cols
 // grid: gx / RB blocks; rows u of Xh (2N cells along v) -> B[i][u] for the N image rows.
+// The RB rows of a block lie in one tile row (RB <= TS).
 template <int N, int RB>
-__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 256 ? 2 : 1) inv_cols_kernel(PatchSrc src, float2* __restrict__ B,
-                                                                int gx, const float2* __restrict__ tw2N) {
+__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv_cols_kernel(PatchSrc src, float2* __restrict__ B,
+                                                                int gx, const float2* __restrict__ tw2N,
+                                                                const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
+    int* s_own = reinterpret_cast<int*>(smem + RB * (N + N / 16));
+    int* s_up = s_own + src.ntv;
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * (N + N / 16);
     const int u = blockIdx.x * RB + g;
+    {
+        const int tu = (blockIdx.x * RB) >> src.shift;
+        const int tu1 = tu == 0 ? src.ntu - 1 : tu - 1;
+        for (int e = threadIdx.x; e < src.ntv; e += blockDim.x) {
+            s_own[e] = __ldg(&src.slot[tu * src.ntv + e]);
+            s_up[e] = __ldg(&src.slot[tu1 * src.ntv + e]);
+        }
+    }
+    __syncthreads();
+    const int au = u & ((1 << src.shift) - 1);
+    const bool hu = au < src.H;
     float2 v[16];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + T * m;
-            float2 a = patch_at(src, u, k), b = patch_at(src, u, k + N);
+            float2 a = fold_cell(src, s_own, s_up, au, hu, k), b = fold_cell(src, s_own, s_up, au, hu, k + N);
             v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
         }
-        fft_n<N, true>(v, sm, t, tw2N);
+        fft_n<N, true>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
         __syncthreads();
@@ -365,9 +401,10 @@ __global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 256 ? 2 : 1) inv
 // ----------------------------------------------------------------------------- inverse rows
 // grid: ny / RG blocks; row i of B (2N cells along u) -> out[i][0 .. N) * conj(Z_p)
 template <int N, int RG>
-__global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (1024 / (RG * N / 16)) : 1) inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out,
+__global__ void __launch_bounds__(RG * N / 16, (768 / (RG * N / 16)) > 0 ? (768 / (RG * N / 16)) : 1) inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out,
                                                                 int ny, ZArgs z, int accumulate, int real_only,
-                                                                const float2* __restrict__ tw2N) {
+                                                                const float2* __restrict__ tw2N,
+                                                                const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
@@ -385,7 +422,7 @@ __global__ void __launch_bounds__(RG * N / 16, (1024 / (RG * N / 16)) > 0 ? (102
             float2 a = __ldg(&in[k]), b = __ldg(&in[k + N]);
             v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
         }
-        fft_n<N, true>(v, sm, t, tw2N);
+        fft_n<N, true>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int mp = t + T * m;
@@ -418,7 +455,7 @@ static ZArgs zargs(const rimo_plan* p, int bin) {
 }
 
 template <int N>
-static constexpr int rows_per_block() { return (N / 16) >= 64 ? 4 : 256 / (N / 16); }
+static constexpr int rows_per_block() { return (N / 16) >= 256 ? 2 : (N / 16) >= 64 ? 4 : 256 / (N / 16); }
 // the inverse cols pass sums up to four patches per input point: fewer rows per block
 // leave it the registers to keep them in flight
 template <int N>
@@ -452,21 +489,23 @@ static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, c
     constexpr int RB = rows_per_block<N>();
     const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
     set_smem(fwd_rows_kernel<N, RB>, sm);
-    fwd_rows_kernel<N, RB><<<p->ny / RB, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x);
+    fwd_rows_kernel<N, RB><<<p->ny / RB, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x, p->tab.tws_x);
 }
 
 template <int N>
-static void fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s) {
+static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
     constexpr int RG = groups_per_block<N>();
-    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2);
+    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2) + 256;
     set_smem(fwd_cols_kernel<N, RG>, sm);
-    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 16, sm, s>>>(At, X, p->tab.tw_y);
+    const size_t ntile = (size_t)(p->gx / p->TS) * (p->gy / p->TS);
+    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 16, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
+                                                                p->TS == 64 ? 6 : 5, p->tab.tw_y, p->tab.tws_y);
 }
 
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     constexpr int RB = inv_rows_per_block<N>();
-    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
+    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 2 * (size_t)(p->gy / p->TS) * sizeof(int);
     set_smem(inv_cols_kernel<N, RB>, sm);
     PatchSrc src;
     src.ntu = p->gx / p->TS;
@@ -476,7 +515,7 @@ static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     src.shift = p->TS == 64 ? 6 : 5;
     src.H = p->H;
     src.PW = p->PW;
-    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(src, B, p->gx, p->tab.tw_y);
+    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(src, B, p->gx, p->tab.tw_y, p->tab.tws_y);
 }
 
 template <int N>
@@ -486,14 +525,14 @@ static void inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, 
     const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2);
     set_smem(inv_rows_kernel<N, RG>, sm);
     inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 16, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re,
-                                                                p->tab.tw_x);
+                                                                p->tab.tw_x, p->tab.tws_x);
 }
 
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
     RIMO_DISPATCH_N(p->nx, fwd_rows<NN>(p, bin, x, At, s));
 }
-void launch_fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s) {
-    RIMO_DISPATCH_N(p->ny, fwd_cols<NN>(p, At, X, s));
+void launch_fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->ny, fwd_cols<NN>(p, bin, At, X, s));
 }
 void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, bin, B, s));

@@ -47,21 +47,22 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// try_wait suspends the thread until the phase completes or about `hint_ns` elapse.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait: gives up after 2^22 suspended polls (seconds); never spins forever.
+// Bounded wait: at most 2^15 suspended polls of <= 100 us (about 3 s); never spins forever.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
+    for (uint32_t it = 0; it < (1u << 15); ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -64,6 +64,8 @@ struct BinRange {
 struct DevTables {
     float2* tw_x = nullptr;    // e^{-2 pi i k / (2 nx)}, k in [0, 2 nx)
     float2* tw_y = nullptr;    // e^{-2 pi i k / (2 ny)}
+    float2* tws_x = nullptr;   // Stockham stage twiddle tables for the nx-point transforms
+    float2* tws_y = nullptr;   // ... and the ny-point transforms
     float* gc_x = nullptr;     // grid correction 1 / KB_hat, per column
     float* gc_y = nullptr;     // per row
     float2* dn = nullptr;      // (sqrt(1-l^2-m^2)-1) as float pairs, [|i_c|][|j_c|], (ny/2+1) x (nx/2+1)
@@ -110,6 +112,7 @@ struct rimo_plan {
     float2* d_X = nullptr;     // forward grid   (gx rows u, gy cols v)
     float2* d_patch = nullptr; // gridded accumulator patch of every active tile of one bin
     int32_t* d_slot = nullptr; // [bin][tu][tv] -> index of the tile's patch in d_patch, or -1
+    uint8_t* d_need = nullptr; // [bin][tu][tv] != 0: some active patch of the bin reads the tile
     int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)
     int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
     int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
@@ -141,7 +144,7 @@ void prof_end(rimo_plan* p, int launches, cudaStream_t s);
 
 // Kernel launchers (defined in the .cu files).
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s);
-void launch_fwd_cols(const rimo_plan* p, const float2* At, float2* X, cudaStream_t s);
+void launch_fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s);
 // reads the gridded grid of bin `bin` as the sum of the overlapping tile patches
 void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s);
 void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,

@@ -139,6 +139,25 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
     };
     p->tab.tw_x = upload(p, twiddles(nx), s);
     p->tab.tw_y = upload(p, twiddles(ny), s);
+    // Stockham stage tables: stage 2 combines NS = 16 points with radix R2, stage 3
+    // NS = 256 with radix R3; entry [r NS + j] = W_{NS R}^{r j} = e^{-2 pi i r j / (NS R)}
+    auto stage_twiddles = [](int N) {
+        const int R2 = N <= 256 ? N / 16 : 16;
+        const int R3 = N <= 256 ? 0 : N / 256;
+        std::vector<float2> t((size_t)std::max(N, 256 + 256 * std::max(R3, 1)), make_float2(0.f, 0.f));
+        auto fill = [&](size_t off, int NS, int R) {
+            for (int r = 0; r < R; ++r)
+                for (int j = 0; j < NS; ++j) {
+                    double a = -2.0 * M_PI * (double)r * j / ((double)NS * R);
+                    t[off + (size_t)r * NS + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+                }
+        };
+        fill(0, 16, R2);
+        if (R3) fill(256, 256, R3);
+        return t;
+    };
+    p->tab.tws_x = upload(p, stage_twiddles(nx), s);
+    p->tab.tws_y = upload(p, stage_twiddles(ny), s);
     auto gc = [&](int n) {
         std::vector<float> g(n);
         for (int j = 0; j < n; ++j) g[j] = (float)(1.0 / kb_hat((double)(j - n / 2) / (2.0 * n), J, p->beta));
@@ -467,6 +486,20 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     const size_t grid_elems = (size_t)gx * gy;
     p->d_X = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
     p->d_slot = upload(p, slot, s);
+    {
+        // tiles of X read by the patch of some active tile: the tile itself and its
+        // neighbours after it along u, v and both (the patch reaches H cells past the tile)
+        std::vector<uint8_t> need((size_t)P * ntile, 0);
+        for (int b = 0; b < P; ++b)
+            for (int tu = 0; tu < ntu; ++tu)
+                for (int tv = 0; tv < ntv; ++tv) {
+                    if (slot[(size_t)b * ntile + (size_t)tu * ntv + tv] < 0) continue;
+                    for (int du = 0; du < 2; ++du)
+                        for (int dv = 0; dv < 2; ++dv)
+                            need[(size_t)b * ntile + (size_t)((tu + du) % ntu) * ntv + (tv + dv) % ntv] = 1;
+                }
+        p->d_need = upload(p, need, s);
+    }
     p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
     p->d_status = (int32_t*)dev_alloc(p, sizeof(int32_t));
