@@ -78,7 +78,7 @@ static void reset_schedulers(rimo_plan* p, cudaStream_t s) {
 static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cudaStream_t s) {
     prof_begin(p, ST_INV_COLS, s);
     launch_inv_cols(p, b, p->d_AB, s);
-    prof_end(p, 1, s);
+    prof_end(p, p->bins[b].n1 > p->bins[b].n0 ? 2 : 1, s);
     prof_begin(p, ST_INV_ROWS, s);
     launch_inv_rows(p, b, p->d_AB, out, first ? 0 : 1, real_only, s);
     prof_end(p, 1, s);
@@ -87,7 +87,8 @@ static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cud
 static void gtg(rimo_plan* p, int b, int mode, const float2* y_in, float2* y_out, cudaStream_t s) {
     prof_begin(p, ST_GTG, s);
     launch_gtg(p, b, mode, y_in, y_out, s);
-    prof_end(p, gtg_launches(p, b, mode), s);
+    const bool merge = mode != 0 && p->bins[b].m1 > p->bins[b].m0;
+    prof_end(p, gtg_launches(p, b, mode) + (merge ? 1 : 0), s);
 }
 
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {

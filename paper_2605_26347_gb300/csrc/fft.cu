@@ -309,74 +309,67 @@ __global__ void __launch_bounds__(RG * N / 16, (768 / (RG * N / 16)) > 0 ? (768 
     }
 }
 
-// The gridded grid of one bin, read as the sum of the accumulator patches of the active
-// uv-tiles that cover a cell (its own tile, and the halos of the tiles before it along u
-// and v); cells no active tile reaches are zero.
-struct PatchSrc {
-    const float2* patch;  // [slot][PW * PW]
-    const int* slot;      // [tu * ntv + tv] -> slot or -1
-    int ntu, ntv, shift, H, PW;
+// ----------------------------------------------------------------------------- patch fold
+// The gridded grid Xh of one bin is the sum of the accumulator patches of its active
+// uv-tiles: a cell gets its own tile's patch and the halos of the tiles before it along u
+// and v.  One block folds one needed tile (TS x TS cells) and writes it to Xh; tiles no
+// patch reaches are never written and read as zero by the inverse transform.
+struct FoldArgs {
+    const float2* patch;   // [slot][PW * PW]
+    const int* slot;       // [tu * ntv + tv] -> slot or -1 (this bin)
+    const int* tiles;      // needed tiles of this bin, tu * ntv + tv
+    float2* Xh;            // [gx][gy]
+    int ntu, ntv, TS, H, PW, gy;
 };
 
-// Fold one cell of row u (tile row tu, offset au) from the patches; s_own / s_up are the
-// slots of tile rows tu and tu - 1, cached in shared memory.
-__device__ __forceinline__ float2 fold_cell(const PatchSrc& P, const int* s_own, const int* s_up, int au,
-                                           bool hu, int v) {
-    const int TS = 1 << P.shift;
-    const int tv = v >> P.shift, av = v & (TS - 1);
-    const size_t np = (size_t)P.PW * P.PW;
-    const int tv1 = tv == 0 ? P.ntv - 1 : tv - 1;
-    const bool hv = av < P.H;
-    float2 acc = make_float2(0.f, 0.f);
-    int s = s_own[tv];
-    if (s >= 0) acc = __ldg(&P.patch[s * np + au * P.PW + av]);
-    if (hv) {
-        s = s_own[tv1];
-        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + au * P.PW + av + TS]));
+__global__ void __launch_bounds__(256) fold_kernel(FoldArgs F) {
+    const int tile = F.tiles[blockIdx.x];
+    const int tu = tile / F.ntv, tv = tile - tu * F.ntv;
+    const int tu1 = tu == 0 ? F.ntu - 1 : tu - 1, tv1 = tv == 0 ? F.ntv - 1 : tv - 1;
+    const size_t np = (size_t)F.PW * F.PW;
+    const int s00 = F.slot[tu * F.ntv + tv], s10 = F.slot[tu1 * F.ntv + tv];
+    const int s01 = F.slot[tu * F.ntv + tv1], s11 = F.slot[tu1 * F.ntv + tv1];
+    for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
+        const int a = e / F.TS, b = e - a * F.TS;
+        float2 acc = make_float2(0.f, 0.f);
+        if (s00 >= 0) acc = F.patch[s00 * np + a * F.PW + b];
+        if (a < F.H && s10 >= 0) acc = cadd(acc, F.patch[s10 * np + (a + F.TS) * F.PW + b]);
+        if (b < F.H && s01 >= 0) acc = cadd(acc, F.patch[s01 * np + a * F.PW + b + F.TS]);
+        if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, F.patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
+        F.Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
     }
-    if (hu) {
-        s = s_up[tv];
-        if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av]));
-        if (hv) {
-            s = s_up[tv1];
-            if (s >= 0) acc = cadd(acc, __ldg(&P.patch[s * np + (au + TS) * P.PW + av + TS]));
-        }
-    }
-    return acc;
 }
 
 // ----------------------------------------------------------------------------- inverse cols
-// grid: gx / RB blocks; rows u of Xh (2N cells along v) -> B[i][u] for the N image rows.
-// The RB rows of a block lie in one tile row (RB <= TS).
+// grid: gx / RB blocks; rows u of Xh (2N cells along v; cells of tiles without a mark in
+// need[] are zero and not read) -> B[i][u] for the N image rows.  The RB rows of a block
+// lie in one tile row (RB <= TS).
 template <int N, int RB>
-__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv_cols_kernel(PatchSrc src, float2* __restrict__ B,
-                                                                int gx, const float2* __restrict__ tw2N,
+__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B,
+                                                                int gx, const uint8_t* __restrict__ need, int shift,
+                                                                const float2* __restrict__ tw2N,
                                                                 const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     extern __shared__ float2 smem[];
-    int* s_own = reinterpret_cast<int*>(smem + RB * (N + N / 16));
-    int* s_up = s_own + src.ntv;
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RB * (N + N / 16));
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * (N + N / 16);
     const int u = blockIdx.x * RB + g;
     {
-        const int tu = (blockIdx.x * RB) >> src.shift;
-        const int tu1 = tu == 0 ? src.ntu - 1 : tu - 1;
-        for (int e = threadIdx.x; e < src.ntv; e += blockDim.x) {
-            s_own[e] = __ldg(&src.slot[tu * src.ntv + e]);
-            s_up[e] = __ldg(&src.slot[tu1 * src.ntv + e]);
-        }
+        const int ntv = (2 * N) >> shift;
+        const uint8_t* nr = need + (size_t)((blockIdx.x * RB) >> shift) * ntv;
+        for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = nr[e];
     }
     __syncthreads();
-    const int au = u & ((1 << src.shift) - 1);
-    const bool hu = au < src.H;
+    const float2* in = Xh + (size_t)u * (2 * N);
     float2 v[16];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + T * m;
-            float2 a = fold_cell(src, s_own, s_up, au, hu, k), b = fold_cell(src, s_own, s_up, au, hu, k + N);
+            const float2 a = s_need[k >> shift] ? __ldg(&in[k]) : make_float2(0.f, 0.f);
+            const float2 b = s_need[(k + N) >> shift] ? __ldg(&in[k + N]) : make_float2(0.f, 0.f);
             v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
         }
         fft_n<N, true>(v, sm, t, tws);
@@ -505,17 +498,27 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     constexpr int RB = inv_rows_per_block<N>();
-    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 2 * (size_t)(p->gy / p->TS) * sizeof(int);
+    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 256;
     set_smem(inv_cols_kernel<N, RB>, sm);
-    PatchSrc src;
-    src.ntu = p->gx / p->TS;
-    src.ntv = p->gy / p->TS;
-    src.patch = p->d_patch;
-    src.slot = p->d_slot + (size_t)bin * src.ntu * src.ntv;
-    src.shift = p->TS == 64 ? 6 : 5;
-    src.H = p->H;
-    src.PW = p->PW;
-    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(src, B, p->gx, p->tab.tw_y, p->tab.tws_y);
+    const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
+    const size_t ntile = (size_t)ntu * ntv;
+    const auto& br = p->bins[bin];
+    if (br.n1 > br.n0) {
+        FoldArgs F;
+        F.patch = p->d_patch;
+        F.slot = p->d_slot + (size_t)bin * ntile;
+        F.tiles = p->d_need_list + br.n0;
+        F.Xh = p->d_X;
+        F.ntu = ntu;
+        F.ntv = ntv;
+        F.TS = p->TS;
+        F.H = p->H;
+        F.PW = p->PW;
+        F.gy = p->gy;
+        fold_kernel<<<br.n1 - br.n0, 256, 0, s>>>(F);
+    }
+    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(p->d_X, B, p->gx, p->d_need + (size_t)bin * ntile,
+                                                                p->TS == 64 ? 6 : 5, p->tab.tw_y, p->tab.tws_y);
 }
 
 template <int N>

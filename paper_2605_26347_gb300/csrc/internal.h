@@ -56,6 +56,7 @@ struct BinRange {
     int64_t vb = 0, ve = 0;       // visibilities of the bin in sorted order
     int32_t t0 = 0, t1 = 0;       // work units of the bin: tiles_host[t0 .. t1) (patch slots 0 ..)
     int32_t m0 = 0, m1 = 0;       // merge groups (split tiles) of the bin: merge_host[m0 .. m1)
+    int32_t n0 = 0, n1 = 0;       // needed tiles of the bin: d_need_list[n0 .. n1)
     float w_hi = 0.f, w_lo = 0.f; // w_stack as a float pair (double-float)
     double w = 0.0;
 };
@@ -113,6 +114,7 @@ struct rimo_plan {
     float2* d_patch = nullptr; // gridded accumulator patch of every active tile of one bin
     int32_t* d_slot = nullptr; // [bin][tu][tv] -> index of the tile's patch in d_patch, or -1
     uint8_t* d_need = nullptr; // [bin][tu][tv] != 0: some active patch of the bin reads the tile
+    int32_t* d_need_list = nullptr;  // per bin: the needed tiles as tu * ntv + tv
     int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)
     int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
     int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
@@ -145,7 +147,8 @@ void prof_end(rimo_plan* p, int launches, cudaStream_t s);
 // Kernel launchers (defined in the .cu files).
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s);
 void launch_fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s);
-// reads the gridded grid of bin `bin` as the sum of the overlapping tile patches
+// folds the tile patches of bin `bin` into the gridded grid (in d_X, no longer needed by
+// then) and runs the inverse cols pass on it
 void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s);
 void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,
                      int real_only, cudaStream_t s);

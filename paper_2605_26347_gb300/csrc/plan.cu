@@ -499,6 +499,14 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
                             need[(size_t)b * ntile + (size_t)((tu + du) % ntu) * ntv + (tv + dv) % ntv] = 1;
                 }
         p->d_need = upload(p, need, s);
+        std::vector<int32_t> nl;
+        for (int b = 0; b < P; ++b) {
+            p->bins[b].n0 = (int32_t)nl.size();
+            for (int64_t t = 0; t < ntile; ++t)
+                if (need[(size_t)b * ntile + t]) nl.push_back((int32_t)t);
+            p->bins[b].n1 = (int32_t)nl.size();
+        }
+        p->d_need_list = upload(p, nl, s);
     }
     p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
