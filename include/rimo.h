@@ -240,6 +240,38 @@ rimo_status rimo_profile_read(rimo_plan_t plan, double* ms, int64_t* launches, i
                               int32_t reset);
 
 /*
+ * Phi^dagger Phi without allocating device memory.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory when they apply
+ * the operator - for example a program whose device memory is wholly owned by another
+ * allocator (a framework's caching pool that has reserved the free memory, so that
+ * cudaMalloc would fail or would have to evict its cache), or a processing loop that must
+ * not call cudaMalloc / cudaFree after its set-up phase because those calls may
+ * synchronise the device and take unbounded time.
+ *
+ * It computes exactly what rimo_apply_phi_adj_phi computes with the same arguments (see
+ * there), but takes every scratch buffer of the apply (half-transformed rows, the
+ * forward / gridded grid, the tile patches, the tile schedulers) from one array of
+ * RIMO_NOALLOC_SCRATCH_BYTES (32 MiB) that the library allocates statically on every
+ * device that loads it and keeps until the process exits.  The call itself performs no
+ * cudaMalloc, cudaFree or other allocating call; the plan's own memory is only read.
+ *
+ * Limit: the plan must fit the array: 8 (6 nx ny + max tiles per w-bin * (TS + H)^2) bytes
+ * plus a little alignment, about nx = ny = 512 at most; larger plans are rejected with
+ * RIMO_ERR_UNSUPPORTED and a message naming the bytes needed.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.
+ * Sharing: every call on a device uses the same array; each call clears what must start
+ * at zero.  Calls whose work overlaps on the GPU (other streams, other threads, other
+ * plans) race on the array and give wrong results: serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED (scratch limit), CUDA.
+ */
+#define RIMO_NOALLOC_SCRATCH_BYTES (32u << 20)
+rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t plan, const rimo_cfloat* x_dev,
+                                           rimo_cfloat* out_dev, int32_t real_part_only,
+                                           void* stream);
+
+/*
  * Device status of a plan: synchronises `stream`, then returns RIMO_ERR_TIMEOUT (and
  * clears the flag) if a kernel of this plan gave up a bounded wait since the last call
  * (its results are then invalid), else RIMO_OK.  Kernels never spin without a bound.
