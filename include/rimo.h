@@ -278,6 +278,42 @@ rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t plan, const rimo_cfloat* 
  */
 rimo_status rimo_plan_status(rimo_plan_t plan, void* stream);
 
+/*
+ * Kernel surrogate (a learned replacement for the stored de-gridding taps; no
+ * counterpart in the paper, which stores G or H or recomputes G on the fly, Section 3.4).
+ * A multilayer perceptron maps the normalised inputs x = (2 phi_u - 1, 2 phi_v - 1,
+ * w_r / w_scale) of a visibility - fractional grid offsets along u and v and residual w -
+ * to its 15 x 15 complex tile: 3 -> 128 -> GELU -> 128 -> GELU -> 450 reals (the 225 real
+ * parts row a along u major, then the 225 imaginary parts).  Weights and activations
+ * enter the tensor cores (tcgen05) in bf16 with FP32 accumulation; Adam keeps FP32
+ * masters.  Parameters as one FP32 vector of RIMO_SURROGATE_NPARAM values: W1 [128][3],
+ * b1 [128], W2 [128][128], b2 [128], W3 [450][128], b3 [450].
+ * Batches: B a positive multiple of 128; x_dev, t_dev, y_dev device FP32 row-major
+ * (B x 3, B x 450, B x 450).  The surrogate owns its device memory.
+ */
+#define RIMO_SURROGATE_NPARAM 75074
+typedef struct rimo_surrogate* rimo_surrogate_t;
+/* New surrogate with weights drawn uniformly in +-1/sqrt(fan_in) from `seed`. */
+rimo_status rimo_surrogate_create(uint64_t seed, rimo_surrogate_t* out);
+rimo_status rimo_surrogate_destroy(rimo_surrogate_t s);
+/* Copy the FP32 master parameters to / from the host (set also resets Adam). */
+rimo_status rimo_surrogate_get_params(rimo_surrogate_t s, float* params);
+rimo_status rimo_surrogate_set_params(rimo_surrogate_t s, const float* params);
+/* y = MLP(x) for a batch, enqueued on `stream`. */
+rimo_status rimo_surrogate_forward(rimo_surrogate_t s, const float* x_dev, int64_t B, float* y_dev,
+                                   void* stream);
+/*
+ * Mean squared error over the batch and the 450 outputs, and its gradient with respect to
+ * every parameter (grads: host, RIMO_SURROGATE_NPARAM values; loss: host; either may be
+ * NULL).  Synchronises `stream`.  Errors: INVALID_ARG, TIMEOUT, CUDA.
+ */
+rimo_status rimo_surrogate_gradients(rimo_surrogate_t s, const float* x_dev, const float* t_dev,
+                                     int64_t B, float* grads, float* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss (host, may be
+ * NULL, then no synchronisation) receives the batch loss before the step. */
+rimo_status rimo_surrogate_train_step(rimo_surrogate_t s, const float* x_dev, const float* t_dev,
+                                      int64_t B, float lr, float* loss, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rimo_last_error(void);
 

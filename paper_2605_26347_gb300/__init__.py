@@ -170,5 +170,87 @@ class Plan:
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 
 
+class Surrogate:
+    """The kernel-surrogate MLP (rimo_surrogate_*): 3 -> 128 -> 128 -> 450, bf16 tensor cores."""
+
+    NPARAM = _lib.SURROGATE_NPARAM
+
+    def __init__(self, seed: int = 0):
+        self._lib = _lib.load()
+        h = C.c_void_p()
+        _lib.check(self._lib.rimo_surrogate_create(int(seed), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rimo_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.NPARAM, np.float32)
+        _lib.check(self._lib.rimo_surrogate_get_params(self._h, p.ctypes.data))
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, np.float32))
+        if p.size != self.NPARAM:
+            raise ValueError("wrong parameter count")
+        _lib.check(self._lib.rimo_surrogate_set_params(self._h, p.ctypes.data))
+
+    @staticmethod
+    def _dev(a, cols):
+        torch = _torch()
+        t = a if hasattr(a, "data_ptr") else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+        if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != cols or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 (B, {cols}) array")
+        return t
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        xd = self._dev(x, 3)
+        y = torch.empty((xd.shape[0], 450), dtype=torch.float32, device=xd.device)
+        _lib.check(self._lib.rimo_surrogate_forward(self._h, xd.data_ptr(), xd.shape[0], y.data_ptr(),
+                                                    _stream_ptr(stream)))
+        return y
+
+    def gradients(self, x, t, stream=None):
+        xd, td = self._dev(x, 3), self._dev(t, 450)
+        g = np.zeros(self.NPARAM, np.float32)
+        loss = C.c_float()
+        _lib.check(self._lib.rimo_surrogate_gradients(self._h, xd.data_ptr(), td.data_ptr(), xd.shape[0],
+                                                      g.ctypes.data, C.byref(loss), _stream_ptr(stream)))
+        return float(loss.value), g
+
+    def train_step(self, x, t, lr: float, want_loss: bool = False, stream=None):
+        xd, td = self._dev(x, 3), self._dev(t, 450)
+        loss = C.c_float()
+        _lib.check(self._lib.rimo_surrogate_train_step(self._h, xd.data_ptr(), td.data_ptr(), xd.shape[0],
+                                                       float(lr), C.byref(loss) if want_loss else None,
+                                                       _stream_ptr(stream)))
+        return float(loss.value) if want_loss else None
+
+
+def unpack_params(p: np.ndarray) -> dict:
+    """Split the flat parameter vector into W1, b1, W2, b2, W3, b3 (FP32 views)."""
+    shapes = (("W1", (128, 3)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (450, 128)),
+              ("b3", (450,)))
+    out, o = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        out[name] = p[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def pack_params(d: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(d[k], np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
 def version() -> str:
     return _lib.load().rimo_version().decode()

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "librimo.so")
 
 RIMO_OK = 0
 N_STAGES = 16
+SURROGATE_NPARAM = 75074
 STAGE_NAMES = ["fwd_rows", "fwd_cols", "grid_clear", "gtg", "inv_cols", "inv_rows", "g_build",
                "h_build", "h_apply", "mlp"]
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "CUDA", 5: "TIMEOUT",
@@ -89,6 +90,13 @@ _PROTOS = {
     "rimo_plan_status": (C.c_int, [_P, _P]),
     "rimo_profile_enable": (C.c_int, [_P, C.c_int32]),
     "rimo_profile_read": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
+    "rimo_surrogate_create": (C.c_int, [C.c_uint64, C.POINTER(_P)]),
+    "rimo_surrogate_destroy": (C.c_int, [_P]),
+    "rimo_surrogate_get_params": (C.c_int, [_P, _P]),
+    "rimo_surrogate_set_params": (C.c_int, [_P, _P]),
+    "rimo_surrogate_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
+    "rimo_surrogate_gradients": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "rimo_surrogate_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

@@ -1,0 +1,603 @@
+// Kernel-surrogate MLP: (phi_u, phi_v, w_r) -> 128 -> GELU -> 128 -> GELU -> 450 reals
+// (the 15 x 15 complex de-gridding tile of a visibility), trained on tiles of the exact
+// method.  bf16 weights and activations feed tcgen05 tensor-core GEMMs with FP32
+// accumulation in tensor memory; the elementwise steps (bias, GELU, loss, derivatives)
+// run on the CUDA cores in FP32; Adam keeps FP32 master weights.
+//
+// Training step on a batch of B samples (B a multiple of 128):
+//   Z1 = X W1^T + b1, H1 = bf16(gelu(Z1))              (CUDA cores, K = 3)
+//   Z2 = H1 W2^T + b2, H2 = bf16(gelu(Z2))              (tcgen05)
+//   Y  = H2 W3^T + b3, dY = 2 (Y - T) / (450 B)          (tcgen05, loss on CUDA cores)
+//   dW3 = bf16(dY)^T H2, dH2 = bf16(dY) W3               (tcgen05, split-K over the batch)
+//   dZ2 = dH2 gelu'(Z2); dW2 = bf16(dZ2)^T H1, dH1 = bf16(dZ2) W2
+//   dZ1 = dH1 gelu'(Z1); dW1 = dZ1^T X                   (CUDA cores)
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "internal.h"
+#include "mlp.h"
+#include "tc.cuh"
+
+namespace rimo {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ void mbar_init_(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc::smem_addr(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+// bounded: at most 2^15 polls of <= 100 us each
+__device__ __forceinline__ bool mbar_wait_(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 15); ++it)
+        if (mbar_try_wait_(bar, parity)) return true;
+    return false;
+}
+
+// --------------------------------------------------------------------------------------
+// C[m][n] (+)= sum_k A[m][k] B[n][k]: A (M x K) and B (N x K) bf16 row-major with K
+// contiguous, C fp32.  Block: 128 threads, tile 128 (m) x up to 256 (n), K staged in
+// chunks of 64 into shared memory in the canonical K-major layout; one thread issues
+// the tcgen05.mma (K = 16 each), the accumulator lives in tensor memory.
+constexpr int GEMM_NT = 256;
+constexpr int GEMM_KC = 64;
+constexpr size_t GEMM_SMEM = 100 * 1024;  // also caps residency at two blocks per SM
+
+struct GemmArgs {
+    const bf16* A;
+    const bf16* B;
+    float* C;
+    int lda, ldb, ldc;
+    int M, N, K;
+    int kspan;   // K range of one split (grid.z)
+    int atomic;  // add into C (split-K) instead of storing
+    int* status;
+};
+
+__global__ void __launch_bounds__(128) gemm_tc_kernel(GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* sA = sm;                          // 128 x 64 bf16 = 16 KB
+    unsigned char* sB = sm + 16384;                  // 256 x 64 bf16 = 32 KB
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * GEMM_NT, m0 = blockIdx.y * 128;
+    const int nt = min(GEMM_NT, g.N - n0);
+    const int k_begin = blockIdx.z * g.kspan, k_end = min(g.K, k_begin + g.kspan);
+    if (warp == 0) tc::tmem_alloc(&tslot, GEMM_NT);
+    if (tid == 0) {
+        mbar_init_(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, nt);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = k_begin; k0 < k_end; k0 += GEMM_KC) {
+        const int kc = min(GEMM_KC, k_end - k0);   // multiple of 16
+        const int nv = kc / 8;                      // 16-byte vectors per row
+        for (int e = tid; e < 128 * nv; e += 128) {
+            const int r = e / nv, v = e - r * nv;
+            const uint4 val = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + v * 8);
+            *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, v * 8, 128)) = val;
+        }
+        for (int e = tid; e < nt * nv; e += 128) {
+            const int r = e / nv, v = e - r * nv;
+            const uint4 val = *reinterpret_cast<const uint4*>(g.B + (size_t)(n0 + r) * g.ldb + k0 + v * 8);
+            *reinterpret_cast<uint4*>(sB + tc::kmajor_offset(r, v * 8, nt)) = val;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            for (int s = 0; s < kc / 16; ++s) {
+                const uint64_t ad = tc::smem_desc(tc::smem_addr(sA) + s * 128 * 32, 128, 256);
+                const uint64_t bd = tc::smem_desc(tc::smem_addr(sB) + s * nt * 32, 128, 256);
+                tc::mma_bf16(tmem, ad, bd, idesc, (k0 > k_begin || s > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar);
+        }
+        ok = mbar_wait_(&bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(g.status, 2);
+    } else if (k_end > k_begin) {
+        tc::fence_after_sync();
+        const int row = m0 + 32 * warp + lane;
+        for (int c = 0; c < nt; c += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
+            float* dst = g.C + (size_t)row * g.ldc + n0 + c;
+            if (g.atomic) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(dst + i, v[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) {
+        tc::tmem_dealloc(tmem, GEMM_NT);
+        tc::tmem_relinquish();
+    }
+}
+
+static void gemm(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 int splits, bool atomic, int* status, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        RIMO_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM));
+        attr = true;
+    }
+    GemmArgs g;
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kspan = ((K / splits + 15) / 16) * 16;
+    g.atomic = atomic ? 1 : 0;
+    g.status = status;
+    dim3 grid((N + GEMM_NT - 1) / GEMM_NT, M / 128, (K + g.kspan - 1) / g.kspan);
+    gemm_tc_kernel<<<grid, 128, GEMM_SMEM, s>>>(g);
+}
+
+// --------------------------------------------------------------------------------------
+// elementwise steps
+__global__ void l1_fwd_kernel(const float* __restrict__ X, const float* __restrict__ W1, const float* __restrict__ b1,
+                              float* __restrict__ Z1, bf16* __restrict__ H1, int B) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)B * MLP_H) return;
+    const int b = (int)(e / MLP_H), j = (int)(e % MLP_H);
+    const float w0 = __bfloat162float(__float2bfloat16(W1[j * 3 + 0]));
+    const float w1 = __bfloat162float(__float2bfloat16(W1[j * 3 + 1]));
+    const float w2 = __bfloat162float(__float2bfloat16(W1[j * 3 + 2]));
+    const float z = fmaf(X[b * 3 + 0], w0, fmaf(X[b * 3 + 1], w1, fmaf(X[b * 3 + 2], w2, b1[j])));
+    Z1[e] = z;
+    H1[e] = __float2bfloat16(gelu_f(z));
+}
+
+// Z (in place) += bias; H = bf16(gelu(Z))
+__global__ void act_fwd_kernel(float* __restrict__ Z, const float* __restrict__ bias, bf16* __restrict__ H, int B,
+                               int n, int ld) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)B * n) return;
+    const int b = (int)(e / n), j = (int)(e % n);
+    const float z = Z[(size_t)b * ld + j] + bias[j];
+    Z[(size_t)b * ld + j] = z;
+    H[(size_t)b * n + j] = __float2bfloat16(gelu_f(z));
+}
+
+// Y += b3; r = Y - T; loss += r^2; dY = 2 r / (450 B) as bf16 (cols >= 450 zero); db3 += dY
+__global__ void loss_bwd_kernel(float* __restrict__ Y, int ldy, const float* __restrict__ b3,
+                                const float* __restrict__ T, bf16* __restrict__ dY, int ld_dy, float* __restrict__ db3,
+                                float* __restrict__ loss, int B) {
+    __shared__ float red[256];
+    const int j = blockIdx.x % MLP_OUT_PAD;  // one output column per block x slice of the batch
+    const int part = blockIdx.x / MLP_OUT_PAD, nparts = gridDim.x / MLP_OUT_PAD;
+    float sq = 0.f, db = 0.f;
+    const float scale = 2.f / ((float)MLP_OUT * (float)B);
+    for (int b = part * blockDim.x + threadIdx.x; b < B; b += nparts * blockDim.x) {
+        float d = 0.f;
+        if (j < MLP_OUT) {
+            const float y = Y[(size_t)b * ldy + j] + b3[j];
+            Y[(size_t)b * ldy + j] = y;
+            const float r = y - T[(size_t)b * MLP_OUT + j];
+            sq += r * r;
+            d = scale * r;
+            db += d;
+        }
+        dY[(size_t)b * ld_dy + j] = __float2bfloat16(d);
+    }
+    red[threadIdx.x] = sq;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && j < MLP_OUT) atomicAdd(loss, red[0]);
+    __syncthreads();
+    red[threadIdx.x] = db;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && j < MLP_OUT) atomicAdd(&db3[j], red[0]);
+}
+
+// dZ = dH * gelu'(Z) -> bf16; db += dZ (fp32)
+__global__ void act_bwd_kernel(const float* __restrict__ dH, const float* __restrict__ Z, bf16* __restrict__ dZ,
+                               float* __restrict__ db, int B) {
+    __shared__ float red[256];
+    const int j = blockIdx.x % MLP_H, part = blockIdx.x / MLP_H, nparts = gridDim.x / MLP_H;
+    float acc = 0.f;
+    for (int b = part * blockDim.x + threadIdx.x; b < B; b += nparts * blockDim.x) {
+        const float d = dH[(size_t)b * MLP_H + j] * gelu_grad_f(Z[(size_t)b * MLP_H + j]);
+        dZ[(size_t)b * MLP_H + j] = __float2bfloat16(d);
+        acc += d;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&db[j], red[0]);
+}
+
+// dZ1 = dH1 * gelu'(Z1); dW1[j][i] += dZ1[b][j] X[b][i]; db1[j] += dZ1[b][j]
+__global__ void l1_bwd_kernel(const float* __restrict__ dH1, const float* __restrict__ Z1, const float* __restrict__ X,
+                              float* __restrict__ dW1, float* __restrict__ db1, int B) {
+    __shared__ float red[4][256];
+    const int j = blockIdx.x % MLP_H, part = blockIdx.x / MLP_H, nparts = gridDim.x / MLP_H;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int b = part * blockDim.x + threadIdx.x; b < B; b += nparts * blockDim.x) {
+        const float d = dH1[(size_t)b * MLP_H + j] * gelu_grad_f(Z1[(size_t)b * MLP_H + j]);
+        a0 += d * X[b * 3 + 0];
+        a1 += d * X[b * 3 + 1];
+        a2 += d * X[b * 3 + 2];
+        a3 += d;
+    }
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    red[3][threadIdx.x] = a3;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&dW1[j * 3 + 0], red[0][0]);
+        atomicAdd(&dW1[j * 3 + 1], red[1][0]);
+        atomicAdd(&dW1[j * 3 + 2], red[2][0]);
+        atomicAdd(&db1[j], red[3][0]);
+    }
+}
+
+// dst[c][r] = src[r][c], bf16, 32 x 32 tiles through shared memory
+__global__ void transpose_bf16_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, int R, int Cn) {
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < R && c < Cn) ? src[(size_t)r * Cn + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < Cn && r < R) dst[(size_t)c * R + r] = t[threadIdx.x][i];
+    }
+}
+
+static void transpose(const bf16* src, bf16* dst, int R, int Cn, cudaStream_t s) {
+    dim3 grid((Cn + 31) / 32, (R + 31) / 32), block(32, 8);
+    transpose_bf16_kernel<<<grid, block, 0, s>>>(src, dst, R, Cn);
+}
+
+// Adam on the FP32 masters, then the bf16 operand copies: W2 [128][128], W2^T, W3 [464][128]
+// (rows >= 450 zero) and W3^T [128][512] (columns >= 450 zero).
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void pack_weights_kernel(const float* __restrict__ P, bf16* __restrict__ W2b, bf16* __restrict__ W2Tb,
+                                    bf16* __restrict__ W3b, bf16* __restrict__ W3Tb) {
+    const float* W2 = P + MLP_OFF_W2;
+    const float* W3 = P + MLP_OFF_W3;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < MLP_H * MLP_H) {
+        const int r = i / MLP_H, c = i % MLP_H;
+        const bf16 w = __float2bfloat16(W2[i]);
+        W2b[i] = w;
+        W2Tb[c * MLP_H + r] = w;
+    }
+    if (i < MLP_OUT_PAD * MLP_H) {
+        const int r = i / MLP_H, c = i % MLP_H;
+        const bf16 w = __float2bfloat16(r < MLP_OUT ? W3[r * MLP_H + c] : 0.f);
+        W3b[i] = w;
+        W3Tb[c * MLP_K3 + r] = w;
+    }
+    if (i < MLP_H * (MLP_K3 - MLP_OUT_PAD)) {
+        const int c = i / (MLP_K3 - MLP_OUT_PAD), r = MLP_OUT_PAD + i % (MLP_K3 - MLP_OUT_PAD);
+        W3Tb[c * MLP_K3 + r] = __float2bfloat16(0.f);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+Mlp::~Mlp() {
+    for (void* p : owned) cudaFree(p);
+}
+
+void* Mlp::alloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        fail(RIMO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes for the surrogate failed");
+    }
+    owned.push_back(p);
+    return p;
+}
+
+void Mlp::init(uint64_t seed) {
+    P = (float*)alloc(MLP_NPARAM * sizeof(float));
+    G = (float*)alloc(MLP_NPARAM * sizeof(float));
+    Mom = (float*)alloc(MLP_NPARAM * sizeof(float));
+    Vel = (float*)alloc(MLP_NPARAM * sizeof(float));
+    W2b = (bf16*)alloc(MLP_H * MLP_H * sizeof(bf16));
+    W2Tb = (bf16*)alloc(MLP_H * MLP_H * sizeof(bf16));
+    W3b = (bf16*)alloc(MLP_OUT_PAD * MLP_H * sizeof(bf16));
+    W3Tb = (bf16*)alloc(MLP_H * MLP_K3 * sizeof(bf16));
+    loss = (float*)alloc(sizeof(float));
+    status = (int*)alloc(sizeof(int));
+    RIMO_CUDA(cudaMemset(status, 0, sizeof(int)));
+    // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from a seeded host generator
+    std::vector<float> h(MLP_NPARAM);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    auto fill = [&](int off, int n, int fan_in) {
+        const double a = 1.0 / std::sqrt((double)fan_in);
+        for (int i = 0; i < n; ++i) h[off + i] = (float)(a * U(rng));
+    };
+    fill(MLP_OFF_W1, MLP_H * MLP_IN, MLP_IN);
+    fill(MLP_OFF_B1, MLP_H, MLP_IN);
+    fill(MLP_OFF_W2, MLP_H * MLP_H, MLP_H);
+    fill(MLP_OFF_B2, MLP_H, MLP_H);
+    fill(MLP_OFF_W3, MLP_OUT * MLP_H, MLP_H);
+    fill(MLP_OFF_B3, MLP_OUT, MLP_H);
+    set_params(h.data(), 0);
+}
+
+void Mlp::set_params(const float* host, cudaStream_t s) {
+    RIMO_CUDA(cudaMemcpyAsync(P, host, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, s));
+    RIMO_CUDA(cudaMemsetAsync(Mom, 0, MLP_NPARAM * sizeof(float), s));
+    RIMO_CUDA(cudaMemsetAsync(Vel, 0, MLP_NPARAM * sizeof(float), s));
+    t = 0;
+    pack(s);
+}
+
+void Mlp::pack(cudaStream_t s) {
+    const int n = MLP_OUT_PAD * MLP_H;
+    pack_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(P, W2b, W2Tb, W3b, W3Tb);
+}
+
+void Mlp::reserve(int B) {
+    if (B <= cap) return;
+    cap = B;
+    Z1 = (float*)alloc((size_t)B * MLP_H * sizeof(float));
+    Z2 = (float*)alloc((size_t)B * MLP_H * sizeof(float));
+    Y = (float*)alloc((size_t)B * MLP_OUT_PAD * sizeof(float));
+    dH = (float*)alloc((size_t)B * MLP_H * sizeof(float));
+    H1 = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+    H1T = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+    H2 = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+    H2T = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+    dY = (bf16*)alloc((size_t)B * MLP_K3 * sizeof(bf16));
+    dYT = (bf16*)alloc((size_t)B * MLP_K3 * sizeof(bf16));
+    dZ = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+    dZT = (bf16*)alloc((size_t)B * MLP_H * sizeof(bf16));
+}
+
+void Mlp::forward(const float* X, int B, cudaStream_t s) {
+    reserve(B);
+    const int n1 = B * MLP_H;
+    l1_fwd_kernel<<<(n1 + 255) / 256, 256, 0, s>>>(X, P + MLP_OFF_W1, P + MLP_OFF_B1, Z1, H1, B);
+    gemm(H1, MLP_H, W2b, MLP_H, Z2, MLP_H, B, MLP_H, MLP_H, 1, false, status, s);
+    act_fwd_kernel<<<(n1 + 255) / 256, 256, 0, s>>>(Z2, P + MLP_OFF_B2, H2, B, MLP_H, MLP_H);
+    gemm(H2, MLP_H, W3b, MLP_H, Y, MLP_OUT_PAD, B, MLP_OUT_PAD, MLP_H, 1, false, status, s);
+}
+
+void Mlp::grads(const float* X, const float* T, int B, cudaStream_t s) {
+    forward(X, B, s);
+    RIMO_CUDA(cudaMemsetAsync(G, 0, MLP_NPARAM * sizeof(float), s));
+    RIMO_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    RIMO_CUDA(cudaMemsetAsync(dY, 0, (size_t)B * MLP_K3 * sizeof(bf16), s));
+    const int parts = std::max(1, std::min(16, B / 256));
+    loss_bwd_kernel<<<MLP_OUT_PAD * parts, 256, 0, s>>>(Y, MLP_OUT_PAD, P + MLP_OFF_B3, T, dY, MLP_K3,
+                                                       G + MLP_OFF_B3, loss, B);
+    transpose(H2, H2T, B, MLP_H, s);
+    transpose(dY, dYT, B, MLP_K3, s);
+    const int splits = std::max(1, B / 512);
+    // dH2 = dY W3 (K = 464 padded output dimension)
+    gemm(dY, MLP_K3, W3Tb, MLP_K3, dH, MLP_H, B, MLP_H, MLP_OUT_PAD, 1, false, status, s);
+    // dW3 = dY^T H2 (M = 464 -> rows >= 450 land in a scratch tail of G3)
+    RIMO_CUDA(cudaMemsetAsync(Y, 0, (size_t)512 * MLP_H * sizeof(float), s));
+    gemm(dYT, B, H2T, B, Y, MLP_H, 512, MLP_H, B, splits, true, status, s);
+    RIMO_CUDA(cudaMemcpyAsync(G + MLP_OFF_W3, Y, (size_t)MLP_OUT * MLP_H * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    act_bwd_kernel<<<MLP_H * parts, 256, 0, s>>>(dH, Z2, dZ, G + MLP_OFF_B2, B);
+    transpose(dZ, dZT, B, MLP_H, s);
+    transpose(H1, H1T, B, MLP_H, s);
+    gemm(dZT, B, H1T, B, G + MLP_OFF_W2, MLP_H, MLP_H, MLP_H, B, splits, true, status, s);
+    gemm(dZ, MLP_H, W2Tb, MLP_H, dH, MLP_H, B, MLP_H, MLP_H, 1, false, status, s);
+    l1_bwd_kernel<<<MLP_H * parts, 256, 0, s>>>(dH, Z1, X, G + MLP_OFF_W1, G + MLP_OFF_B1, B);
+}
+
+void Mlp::step(const float* X, const float* T, int B, float lr, cudaStream_t s) {
+    grads(X, T, B, s);
+    ++t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)t), c2 = 1.f - std::pow(b2, (float)t);
+    adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(P, G, Mom, Vel, MLP_NPARAM, lr, b1, b2, 1e-8f, c1, c2);
+    pack(s);
+}
+
+}  // namespace rimo
+
+// --------------------------------------------------------------------------------------
+// C ABI
+struct rimo_surrogate {
+    rimo::Mlp mlp;
+};
+
+namespace rimo {
+
+__global__ void add_bias_out_kernel(const float* __restrict__ Y, const float* __restrict__ b3, float* __restrict__ out,
+                                    int B) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)B * MLP_OUT) return;
+    const int b = (int)(e / MLP_OUT), j = (int)(e % MLP_OUT);
+    out[e] = Y[(size_t)b * MLP_OUT_PAD + j] + b3[j];
+}
+
+static void check_batch(int64_t B) {
+    if (B <= 0 || B % 128 != 0 || B > (1 << 24)) fail(RIMO_ERR_INVALID_ARG, "batch must be a positive multiple of 128");
+}
+
+static void check_status(Mlp& m, cudaStream_t s) {
+    int st = 0;
+    RIMO_CUDA(cudaMemcpyAsync(&st, m.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RIMO_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        RIMO_CUDA(cudaMemsetAsync(m.status, 0, sizeof(int), s));
+        fail(RIMO_ERR_TIMEOUT, "a bounded tensor-core wait ran out");
+    }
+}
+
+}  // namespace rimo
+
+using namespace rimo;
+
+#define SUR_BEGIN try {
+#define SUR_END                       \
+    return RIMO_OK;                   \
+    }                                 \
+    catch (const Error& e) {          \
+        set_last_error(e.msg);        \
+        return e.status;              \
+    }                                 \
+    catch (const std::exception& e) { \
+        set_last_error(e.what());     \
+        return RIMO_ERR_OOM;          \
+    }
+
+extern "C" {
+
+rimo_status rimo_surrogate_create(uint64_t seed, rimo_surrogate_t* out) {
+    if (out) *out = nullptr;
+    rimo_surrogate* s = nullptr;
+    try {
+        if (!out) fail(RIMO_ERR_INVALID_ARG, "null output");
+        s = new rimo_surrogate();
+        s->mlp.init(seed);
+        RIMO_CUDA(cudaDeviceSynchronize());
+        *out = s;
+        return RIMO_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        delete s;
+        return e.status;
+    }
+}
+
+rimo_status rimo_surrogate_destroy(rimo_surrogate_t s) {
+    delete s;
+    return RIMO_OK;
+}
+
+rimo_status rimo_surrogate_get_params(rimo_surrogate_t s, float* params) {
+    SUR_BEGIN
+    if (!s || !params) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    RIMO_CUDA(cudaMemcpy(params, s->mlp.P, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    SUR_END
+}
+
+rimo_status rimo_surrogate_set_params(rimo_surrogate_t s, const float* params) {
+    SUR_BEGIN
+    if (!s || !params) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    s->mlp.set_params(params, 0);
+    RIMO_CUDA(cudaDeviceSynchronize());
+    SUR_END
+}
+
+rimo_status rimo_surrogate_forward(rimo_surrogate_t s, const float* x, int64_t B, float* y, void* stream) {
+    SUR_BEGIN
+    if (!s || !x || !y) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    check_batch(B);
+    cudaStream_t st = (cudaStream_t)stream;
+    s->mlp.forward(x, (int)B, st);
+    const int64_t n = B * MLP_OUT;
+    add_bias_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->mlp.Y, s->mlp.P + MLP_OFF_B3, y, (int)B);
+    RIMO_CUDA(cudaGetLastError());
+    SUR_END
+}
+
+rimo_status rimo_surrogate_gradients(rimo_surrogate_t s, const float* x, const float* t, int64_t B, float* grads,
+                                     float* loss, void* stream) {
+    SUR_BEGIN
+    if (!s || !x || !t) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    check_batch(B);
+    cudaStream_t st = (cudaStream_t)stream;
+    s->mlp.grads(x, t, (int)B, st);
+    RIMO_CUDA(cudaGetLastError());
+    check_status(s->mlp, st);
+    if (grads) RIMO_CUDA(cudaMemcpy(grads, s->mlp.G, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss) {
+        float l = 0.f;
+        RIMO_CUDA(cudaMemcpy(&l, s->mlp.loss, sizeof(float), cudaMemcpyDeviceToHost));
+        *loss = l / ((float)B * MLP_OUT);
+    }
+    SUR_END
+}
+
+rimo_status rimo_surrogate_train_step(rimo_surrogate_t s, const float* x, const float* t, int64_t B, float lr,
+                                      float* loss, void* stream) {
+    SUR_BEGIN
+    if (!s || !x || !t) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    check_batch(B);
+    cudaStream_t st = (cudaStream_t)stream;
+    s->mlp.step(x, t, (int)B, lr, st);
+    RIMO_CUDA(cudaGetLastError());
+    if (loss) {
+        float l = 0.f;
+        RIMO_CUDA(cudaMemcpyAsync(&l, s->mlp.loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+        RIMO_CUDA(cudaStreamSynchronize(st));
+        *loss = l / ((float)B * MLP_OUT);
+    }
+    SUR_END
+}
+
+}  // extern "C"

@@ -297,3 +297,44 @@ def test_rectangular_image_and_field_against_direct_equation():
     yr = rng.standard_normal(300) + 1j * rng.standard_normal(300)
     xa = direct.direct_phi_adj(yr, uvw, nx, ny, fx, fy)
     assert rel(O.phi_adj(yr), xa) < 3e-4
+
+
+# ---------------------------------------------------------------- surrogate MLP oracle
+def test_mlp_gradients_match_central_differences():
+    from oracle import mlp
+    p = mlp.init_params(3)
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-1, 1, (7, 3))
+    t = rng.standard_normal((7, mlp.D_OUT)) * 0.1
+    _, g = mlp.loss_and_grads(p, x, t)
+    h = 1e-6
+    for name, picks in (("W1", [(0, 0), (5, 2), (127, 1)]), ("b1", [(3,), (100,)]),
+                        ("W2", [(0, 0), (64, 17), (127, 127)]), ("b2", [(9,)]),
+                        ("W3", [(0, 0), (200, 64), (449, 127)]), ("b3", [(0,), (449,)])):
+        for ij in picks:
+            q = {k: v.copy() for k, v in p.items()}
+            q[name][ij] += h
+            lp, _ = mlp.loss_and_grads(q, x, t)
+            q[name][ij] -= 2 * h
+            lm, _ = mlp.loss_and_grads(q, x, t)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[name][ij]) <= 1e-6 * max(1e-3, abs(fd)), (name, ij, fd, g[name][ij])
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    from oracle import mlp
+    # 1 + 2^-8 is halfway between bf16 neighbours 1 and 1 + 2^-7: ties go to the even 1
+    assert mlp.bf16(np.float32(1.0 + 2.0 ** -8)) == 1.0
+    assert mlp.bf16(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
+    assert mlp.bf16(np.float32(-2.5)) == -2.5
+    x = np.random.default_rng(1).standard_normal(1000).astype(np.float32)
+    y = mlp.bf16(x)
+    assert np.max(np.abs(y - x) / np.abs(x)) <= 2.0 ** -8 + 1e-12  # unit roundoff of 8 significant bits
+
+
+def test_gelu_gradient_matches_difference_quotient():
+    from oracle import mlp
+    z = np.linspace(-6, 6, 101)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
