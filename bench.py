@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--bins", type=int, default=32)
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error sample and CPU baseline")
     ap.add_argument("--cpu-sample-vis", type=int, default=20000)
+    ap.add_argument("--tile", type=int, default=0, help="uv-tile size (0: library default)")
     return ap.parse_args()
 
 
@@ -248,7 +249,8 @@ def run_rimo(args):
         dist.init_process_group("nccl")
     uvw, sky, t_synth = workload(args)
     fov = math.radians(3.0)
-    params = pkg.default_params(args.n, args.n, fov, fov, n_wbins=args.bins, mode=pkg.MODE_STORED_G)
+    params = pkg.default_params(args.n, args.n, fov, fov, n_wbins=args.bins, mode=pkg.MODE_STORED_G,
+                                tile_size=args.tile)
     t0 = time.time()
     plan = pkg.Plan(uvw, params)
     t_plan = time.time() - t0

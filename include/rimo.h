@@ -87,7 +87,7 @@ typedef enum rimo_n_weight {
  *   seed              seed of the planning subset.
  *   taper_literal     0: taper the chirp's deviation from 1 (default); 1: taper C.
  *   wkernel_L         w-kernel sampling grid per axis (0 = max(32, 2^ceil(log2(4 S_w,max)))).
- *   tile_size         uv-tile edge in grid cells for sorting/gridding (0 = 64; 32 or 64).
+ *   tile_size         uv-tile edge in grid cells for sorting/gridding (0 = 32; 32 or 64).
  *   block_bytes_max   upper bound of one Fourier block of G (0 = 8 GiB).
  */
 typedef struct rimo_plan_params {
@@ -272,9 +272,11 @@ rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t plan, const rimo_cfloat* 
                                            void* stream);
 
 /*
- * Device status of a plan: synchronises `stream`, then returns RIMO_ERR_TIMEOUT (and
- * clears the flag) if a kernel of this plan gave up a bounded wait since the last call
- * (its results are then invalid), else RIMO_OK.  Kernels never spin without a bound.
+ * Device status of a plan: synchronises `stream`, then returns (and clears the flag)
+ * RIMO_ERR_TIMEOUT if a kernel of this plan gave up a bounded wait, or RIMO_ERR_INVALID_ARG
+ * if an input of Phi^dagger or Phi^dagger Phi held a non-finite value (the grid step
+ * accumulates in fixed point from a bound on its inputs), since the last call - results
+ * are then invalid - else RIMO_OK.  Kernels never spin without a bound.
  */
 rimo_status rimo_plan_status(rimo_plan_t plan, void* stream);
 

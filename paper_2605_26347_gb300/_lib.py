@@ -15,7 +15,7 @@ RIMO_OK = 0
 N_STAGES = 16
 SURROGATE_NPARAM = 75074
 STAGE_NAMES = ["fwd_rows", "fwd_cols", "grid_clear", "gtg", "inv_cols", "inv_rows", "g_build",
-               "h_build", "h_apply", "mlp"]
+               "h_build", "h_apply", "mlp", "bound"]
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "CUDA", 5: "TIMEOUT",
           6: "UNSUPPORTED", 7: "STATE"}
 MODE_AUTO, MODE_STORED_G, MODE_HOLOGRAPHIC, MODE_SURROGATE, MODE_ONTHEFLY = 0, 1, 2, 3, 4

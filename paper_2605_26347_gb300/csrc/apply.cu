@@ -103,6 +103,9 @@ void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {
 void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
     bool first = true;
     reset_schedulers(p, s);
+    prof_begin(p, ST_BOUND, s);
+    launch_y_bound(p, y, s);
+    prof_end(p, p->M > 0 ? 1 : 0, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
         gtg(p, b, 1, y, nullptr, s);
@@ -115,6 +118,9 @@ void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
 void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s) {
     bool first = true;
     reset_schedulers(p, s);
+    prof_begin(p, ST_BOUND, s);
+    launch_image_bound(p, x, s);
+    prof_end(p, 1, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
         fwd(p, b, x, s);
@@ -217,6 +223,7 @@ rimo_status rimo_plan_status(rimo_plan_t p, void* stream) {
     if (flag != 0) {
         RIMO_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s));
         RIMO_CUDA(cudaStreamSynchronize(s));
+        if (flag == 3) fail(RIMO_ERR_INVALID_ARG, "non-finite input values (or a fixed-point bound overflowed)");
         fail(RIMO_ERR_TIMEOUT, "a bounded device wait ran out (code " + std::to_string(flag) + ")");
     }
     RIMO_API_END

@@ -225,6 +225,64 @@ __device__ __forceinline__ float2 z_factor(const ZArgs& z, int i, int j, int ic,
     return make_float2(ph.x * g, ph.y * g);
 }
 
+// ----------------------------------------------------------------------------- bound
+// Bound on the grid-step contributions of Phi^dagger Phi x.  Every forward-grid value of
+// every w-bin is a sum of Z_p x over the pixels with unit-modulus twiddles, and the
+// w-phase has unit modulus, so |X| <= B_x = sum_l (|x_l.re| + |x_l.im|) |Z_l|; a
+// de-gridded y_k then has |y_k.x| + |y_k.y| <= sqrt(2) T1 B_x (T1 = max tap sum), and a
+// contribution component at most tmax times that.  2 tmax T1 B_x goes to
+// d_fx[FX_MAXTERM].  Per-block partial sums are added by the last block in block order
+// (the bound, hence the scales, do not depend on timing).  Non-finite x sets status 3.
+__global__ void __launch_bounds__(256) image_bound_kernel(const float2* __restrict__ x, int nx, int ny, ZArgs z,
+                                                          uint32_t* fx, int* status) {
+    __shared__ float red[256];
+    __shared__ bool last;
+    float acc = 0.f;
+    bool bad = false;
+    const int n = nx * ny;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int i = e / nx, j = e - i * nx;
+        float g = __ldg(&z.gcx[j]) * __ldg(&z.gcy[i]);
+        if (z.div_n) {
+            const float2 d = __ldg(&z.dn[abs(i - ny / 2) * z.dn_ld + abs(j - nx / 2)]);
+            g = g / (1.0f + (d.x + d.y));
+        }
+        const float2 v = x[e];
+        const float m = fabsf(v.x) + fabsf(v.y);
+        bad |= !(m <= 3.4028234e38f);
+        acc = fmaf(m, fabsf(g), acc);
+    }
+    if (bad) atomicExch(status, 3);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        reinterpret_cast<float*>(fx + FX_PART)[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(fx + FX_COUNT, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    float t = 0.f;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(reinterpret_cast<const float*>(fx + FX_PART) + b);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float mt = 2.f * __uint_as_float(__ldcg(fx + FX_TMAX)) * __uint_as_float(__ldcg(fx + FX_T1)) * red[0];
+        if (!(mt <= 3.4028234e38f)) atomicExch(status, 3);
+        fx[FX_MAXTERM] = __float_as_uint(mt);
+        fx[FX_COUNT] = 0u;
+    }
+}
+
 // ----------------------------------------------------------------------------- forward rows
 // grid: ny / RB blocks of RB * N/16 threads; block b transforms image rows [b RB, b RB + RB).
 template <int N, int RB>
@@ -445,6 +503,12 @@ static ZArgs zargs(const rimo_plan* p, int bin) {
     z.w_lo = p->bins[bin].w_lo;
     z.div_n = p->prm.n_weight == RIMO_NWEIGHT_DIV_N;
     return z;
+}
+
+void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s) {
+    const int64_t n = (int64_t)p->nx * p->ny;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, std::min<int64_t>(FX_NPART, 4 * (int64_t)p->n_sm));
+    image_bound_kernel<<<blocks, 256, 0, s>>>(x, p->nx, p->ny, zargs(p, 0), p->d_fx, p->d_status);
 }
 
 template <int N>

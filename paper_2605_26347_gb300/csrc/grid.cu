@@ -25,12 +25,6 @@
 
 namespace rimo {
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // e / S for e < 400, S <= 19 by multiply-shift with ceil(2^16 / S)
 __device__ __forceinline__ int div_small(int e, int magic) { return (e * magic) >> 16; }
 
@@ -96,6 +90,7 @@ struct GtgArgs {
     int chunk_bytes;
     int nbuf;               // ring depth in use, 2..GTG_NBUF
     int* status;
+    const uint32_t* fx;     // fixed-point bounds (maxterm of this apply)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -109,69 +104,123 @@ __device__ __forceinline__ void consumers_sync() {
 // unit processed by block c in round r: snake order over the heaviest-first schedule
 __device__ __forceinline__ int unit_of(int r, int c, int G) { return r * G + ((r & 1) ? (G - 1 - c) : c); }
 
-// One visibility by one warp, tile side S known at compile time.  Lane = (row parity,
-// column): half-warp h takes rows h, h + 2, ...; column c (and c + 16 when S > 16).
-// The taps stay in registers between the de-grid and the grid step.
+// rint by the 1.5 x 2^23 shift: for |d| < 2^22, d + FX_MAGIC has unit spacing, so its bits
+// minus those of FX_MAGIC are rint(d) (round to nearest even)
+constexpr float FX_MAGIC = 12582912.0f;
+constexpr int FX_MAGIC_BITS = 0x4B400000;
+
+// Scale of one work unit of n visibilities: the largest power of two s with
+// s maxterm <= min(2^21, 2^30 / n) (see the fixed-point layout in internal.h).
+__device__ __forceinline__ void fx_scale(float maxterm, int64_t n, float& s1, float& inv) {
+    s1 = 1.f;
+    inv = 1.f;
+    if (!(maxterm > 0.f)) return;  // all contributions vanish (or the input was flagged)
+    const float lim = fminf(2097152.f, 1073741824.f / (float)(n > 1 ? n : 1));
+    int ex = (int)((__float_as_uint(lim / maxterm) >> 23) & 255u) - 127;
+    ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
+    s1 = __uint_as_float((uint32_t)(ex + 127) << 23);
+    inv = __uint_as_float((uint32_t)(127 - ex) << 23);
+}
+
+// One visibility by one warp, tile side S known at compile time.
+// Lane = (cell column, component): lane 2c + k handles column c of a tap row and the real
+// (k = 0) or imaginary (k = 1) part, so one instruction covers one row of up to 16 cells
+// (two rows of up to 8 cells when S <= 8): the shared-memory loads of a row are 16
+// consecutive complex cells and each grid-step reduction 32 consecutive words, both free
+// of bank conflicts.  With a = (t.x, t.y)[k], b = (t.y, t.x)[k]:
+//   de-grid:  Re(t x) = sum a x.x - sum b x.y  (k = 0),  Im(t x) = sum a x.x + sum b x.y  (k = 1);
+//   grid:     component k of conj(t) y = a (+-y.x) + b y.y  (sign + for k = 0, - for k = 1),
+//             times the unit's scale s1, added to the fixed-point patch words hi / lo with
+//             32-bit integer reductions.
+// Both parity classes of lanes reduce with four butterfly steps; one more exchange gives
+// every lane y.  Taps stay in registers between the two steps when S <= 16.
 template <int S, int MODE>
 __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const float2* __restrict__ Xs,
-                                         float2* As, int pbase, int PW, int lane, uint32_t orig,
+                                         int* Ahi, int* Alo, float s1, int pbase, int PW, int lane, uint32_t orig,
                                          const float2* __restrict__ y_in, float2* __restrict__ y_out) {
     constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
-    constexpr int NR = (S + 1) / 2, NC = (S + 15) / 16;
-    const int half = lane >> 4, col = lane & 15;
-    const float2* Tl = T + half * S + col;
-    const int xl = pbase + half * PW + col;
-    float2 t[NR][NC];
-    float ar = 0.f, ai = 0.f;
+    constexpr int RPI = S <= 8 ? 2 : 1;         // tap rows per instruction
+    constexpr int CW = 16 / RPI;                // cells per row and instruction
+    constexpr int NCG = (S + CW - 1) / CW;      // column groups
+    constexpr int NI = (S + RPI - 1) / RPI;     // row steps
+    constexpr bool KEEP = NI * NCG <= 16;       // keep (a, b) in registers for the grid step
+    const int k = lane & 1;
+    const int c = (lane % (2 * CW)) >> 1;
+    const int roff = lane / (2 * CW);
+    const float2* Tl = T + roff * S + c;
+    const int xl = pbase + roff * PW + c;
+    float2 ab[KEEP ? NI : 1][KEEP ? NCG : 1];
+    float acc1 = 0.f, acc2 = 0.f;
 #pragma unroll
-    for (int i = 0; i < NR; ++i)
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const bool ok = (2 * i + half < S) && (col + 16 * j < S);
-            t[i][j] = ok ? Tl[2 * i * S + 16 * j] : make_float2(0.f, 0.f);
+        for (int j = 0; j < NCG; ++j) {
+            const bool ok = (i * RPI + roff < S) && (c + j * CW < S);
+            float2 t = ok ? Tl[i * RPI * S + j * CW] : make_float2(0.f, 0.f);
+            const float2 e = make_float2(k ? t.y : t.x, k ? t.x : t.y);
+            if (KEEP) ab[KEEP ? i : 0][KEEP ? j : 0] = e;
             if (GATHER && ok) {
-                const float2 x = Xs[xl + 2 * i * PW + 16 * j];
-                ar = fmaf(t[i][j].x, x.x, fmaf(-t[i][j].y, x.y, ar));
-                ai = fmaf(t[i][j].x, x.y, fmaf(t[i][j].y, x.x, ai));
+                const float2 x = Xs[xl + i * RPI * PW + j * CW];
+                acc1 = fmaf(e.x, x.x, acc1);
+                acc2 = fmaf(e.y, x.y, acc2);
             }
         }
     float2 y;
     if (GATHER) {
-        y.x = warp_sum(ar);
-        y.y = warp_sum(ai);
+        float v = k ? acc1 + acc2 : acc1 - acc2;
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        const float o = __shfl_xor_sync(0xffffffffu, v, 1);
+        y = k ? make_float2(o, v) : make_float2(v, o);
         if (MODE == 0 && lane == 0) y_out[orig] = y;
     } else {
         y = y_in[orig];
     }
     if (SCATTER) {
+        const float ysx = (k ? -y.x : y.x) * s1, yys = y.y * s1;
 #pragma unroll
-        for (int i = 0; i < NR; ++i)
+        for (int i = 0; i < NI; ++i)
 #pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const bool ok = (2 * i + half < S) && (col + 16 * j < S);
+            for (int j = 0; j < NCG; ++j) {
+                const bool ok = (i * RPI + roff < S) && (c + j * CW < S);
                 if (ok) {
-                    float* a = reinterpret_cast<float*>(&As[xl + 2 * i * PW + 16 * j]);
-                    atomicAdd(a, fmaf(t[i][j].x, y.x, t[i][j].y * y.y));  // conj(t) y
-                    atomicAdd(a + 1, fmaf(t[i][j].x, y.y, -t[i][j].y * y.x));
+                    float2 e;
+                    if (KEEP) {
+                        e = ab[KEEP ? i : 0][KEEP ? j : 0];
+                    } else {
+                        const float2 t = Tl[i * RPI * S + j * CW];
+                        e = make_float2(k ? t.y : t.x, k ? t.x : t.y);
+                    }
+                    // scaled contribution, |d| <= 2^21, split into rint(d) and 2^16 x residual
+                    const float d = fmaf(e.x, ysx, e.y * yys);
+                    const float tq = __fadd_rn(d, FX_MAGIC);
+                    const int q1 = __float_as_int(tq) - FX_MAGIC_BITS;
+                    const float rf = __fsub_rn(d, __fsub_rn(tq, FX_MAGIC));
+                    const int q2 = __float_as_int(__fmaf_rn(rf, 65536.f, FX_MAGIC)) - FX_MAGIC_BITS;
+                    const int ci = 2 * (xl + i * RPI * PW + j * CW) + k;
+                    atomicAdd(Ahi + ci, q1);
+                    atomicAdd(Alo + ci, q2);
                 }
             }
     }
 }
 
 template <int MODE>
-__device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float2* Xs, float2* As, int pbase,
-                                             int PW, int lane, uint32_t orig, const float2* y_in,
+__device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float2* Xs, int* Ahi, int* Alo, float s1,
+                                             int pbase, int PW, int lane, uint32_t orig, const float2* y_in,
                                              float2* y_out) {
     switch (S) {
-        case 3: vis_tile<3, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 5: vis_tile<5, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 7: vis_tile<7, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 9: vis_tile<9, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 11: vis_tile<11, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 13: vis_tile<13, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 15: vis_tile<15, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        case 17: vis_tile<17, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
-        default: vis_tile<19, MODE>(T, Xs, As, pbase, PW, lane, orig, y_in, y_out); break;
+        case 3: vis_tile<3, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 5: vis_tile<5, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 7: vis_tile<7, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 9: vis_tile<9, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 11: vis_tile<11, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 13: vis_tile<13, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 15: vis_tile<15, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 17: vis_tile<17, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        default: vis_tile<19, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
     }
 }
 
@@ -182,8 +231,8 @@ __device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float
 //                   released the slot;
 //   consumer warps: wait full[b]; each takes one visibility of the chunk, de-grids it
 //                   and grids conj(taps) y_k into the block's shared accumulator patch
-//                   (shared-memory atomic adds: visibilities of different warps may
-//                   overlap); then arrive on empty[b].
+//                   (shared-memory reductions, one tap row per instruction:
+//                   visibilities of different warps may overlap); then arrive on empty[b].
 // Only unit boundaries (patch load / store) synchronise all consumers.
 template <int MODE>  // 0: de-grid (y_out), 1: grid (y_in), 2: fused de-grid + grid
 __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
@@ -197,7 +246,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     const int chunk_f2 = A.chunk_bytes / 8;
     const uint32_t NB = (uint32_t)A.nbuf;
     float2* Xs = taps + (size_t)NB * chunk_f2;
-    float2* As = Xs + (GATHER ? npatch : 0);
+    int* Ahi = reinterpret_cast<int*>(Xs + (GATHER ? npatch : 0));  // [cell][re, im] words
+    int* Alo = Ahi + (SCATTER ? 2 * npatch : 0);
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -253,6 +303,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         const TileDesc td = A.units[slot];
         const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
+        float s1 = 1.f, inv_s1 = 1.f;
+        if (SCATTER) fx_scale(__uint_as_float(__ldg(A.fx + FX_MAXTERM)), td.ve - td.vb, s1, inv_s1);
         for (int a = warp; a < PW; a += GTG_CONSUMERS) {
             int gu = u0 + a;
             if (gu >= A.gx) gu -= A.gx;
@@ -262,7 +314,10 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                     if (gv >= A.gy) gv -= A.gy;
                     Xs[a * PW + b] = A.X[(size_t)gu * A.gy + gv];
                 }
-                if (SCATTER) As[a * PW + b] = make_float2(0.f, 0.f);
+                if (SCATTER) {
+                    reinterpret_cast<int2*>(Ahi)[a * PW + b] = make_int2(0, 0);
+                    reinterpret_cast<int2*>(Alo)[a * PW + b] = make_int2(0, 0);
+                }
             }
         }
         consumers_sync();
@@ -278,7 +333,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 const VisMeta mt = mring[b * GTG_CV + warp];
                 const int du = mt.pos & 255, dv = (mt.pos >> 8) & 255, S = (mt.pos >> 16) & 255;
                 const int loc = (int)(mt.off - mring[b * GTG_CV].off);
-                vis_dispatch<MODE>(S, taps + (size_t)b * chunk_f2 + loc, Xs, As, du * PW + dv, PW, lane,
+                vis_dispatch<MODE>(S, taps + (size_t)b * chunk_f2 + loc, Xs, Ahi, Alo, s1, du * PW + dv, PW, lane,
                                    mt.orig, A.y_in, A.y_out);
             }
             __syncwarp();
@@ -287,7 +342,12 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         consumers_sync();
         if (SCATTER && !s_abort) {
             float2* dst = A.patch + (size_t)slot * npatch;
-            for (int e = tid; e < npatch; e += GTG_CONSUMERS * 32) dst[e] = As[e];
+            const float inv_lo = inv_s1 * (1.f / 65536.f);
+            for (int e = tid; e < npatch; e += GTG_CONSUMERS * 32) {
+                const int2 h = reinterpret_cast<const int2*>(Ahi)[e], l = reinterpret_cast<const int2*>(Alo)[e];
+                dst[e] = make_float2(fmaf((float)l.x, inv_lo, (float)h.x * inv_s1),
+                                     fmaf((float)l.y, inv_lo, (float)h.y * inv_s1));
+            }
         }
         consumers_sync();
     }
@@ -311,8 +371,9 @@ __global__ void __launch_bounds__(256) merge_patches_kernel(float2* __restrict__
 
 size_t gtg_smem(const rimo_plan* p, int mode, int nbuf) {
     const size_t npatch = (size_t)p->PW * p->PW * sizeof(float2);
+    // X patch (float2) when de-gridding, hi + lo words (2 x int2) when gridding
     return 128 + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * p->chunk_bytes +
-           (mode == 2 ? 2 : 1) * npatch;
+           (size_t)((mode != 1 ? 1 : 0) + (mode != 0 ? 2 : 0)) * npatch;
 }
 
 template <int MODE>
@@ -337,6 +398,7 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.PW = p->PW;
     A.chunk_bytes = p->chunk_bytes;
     A.status = p->d_status;
+    A.fx = p->d_fx;
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
     A.nbuf = GTG_NBUF;
     while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf) > limit) --A.nbuf;
@@ -354,6 +416,47 @@ void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float
     if (mode == 0) gtg_run<0>(p, bin, y_in, y_out, s);
     else if (mode == 1) gtg_run<1>(p, bin, y_in, y_out, s);
     else gtg_run<2>(p, bin, y_in, y_out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Bound on the grid-step contributions of Phi^dagger y: every contribution component is
+// at most max_taps(|t.x| + |t.y|) * max_k(|y_k.x| + |y_k.y|); twice that (rounding margin)
+// goes to d_fx[FX_MAXTERM].  Non-finite y sets status 3.  The last block to finish
+// (counter in d_fx[FX_COUNT]) writes the bound and resets the running words.
+__global__ void __launch_bounds__(256) y_bound_kernel(const float2* __restrict__ y, int64_t M, uint32_t* fx,
+                                                      int* status) {
+    float mx = 0.f;
+    bool bad = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = y[k];
+        const float m = fabsf(v.x) + fabsf(v.y);
+        bad |= !(m <= 3.4028234e38f);
+        mx = fmaxf(mx, m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(fx + FX_YMAX, __float_as_uint(mx));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(status, 3);
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(fx + FX_COUNT, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const float ym = __uint_as_float(atomicExch(fx + FX_YMAX, 0u));
+        const float mt = 2.f * __uint_as_float(__ldcg(fx + FX_TMAX)) * ym;
+        if (!(mt <= 3.4028234e38f)) atomicExch(status, 3);
+        fx[FX_MAXTERM] = __float_as_uint(mt);
+        fx[FX_COUNT] = 0u;
+    }
+}
+
+void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s) {
+    if (p->M == 0) return;
+    const int64_t want = (p->M + 255) / 256;
+    const int blocks = (int)std::min<int64_t>(want, std::min<int64_t>(FX_NPART, 4 * (int64_t)p->n_sm));
+    y_bound_kernel<<<blocks, 256, 0, s>>>(y, p->M, p->d_fx, p->d_status);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,6 +481,7 @@ struct BuildArgs {
     int kb_nterm;
     int L, hmax, J, literal;
     int64_t nvis;
+    uint32_t* fx;
 };
 
 __device__ __forceinline__ float kb_eval(float t, float invhalf, const float* coef, int nterm) {
@@ -416,7 +520,9 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
     float* taps = reinterpret_cast<float*>(Ab + 9 * 19);  // wu[0..15], wv[16..31]
     const float invL2 = 1.f / ((float)L * (float)L);
     const float invhalf = 2.f / (float)A.J;
+    float tmax = 0.f;
     for (int64_t k = (int64_t)blockIdx.x * BUILD_WARPS + warp; k < A.nvis; k += (int64_t)gridDim.x * BUILD_WARPS) {
+        float tsum = 0.f;
         const VisMeta mt = A.meta[k];
         const int S = (mt.pos >> 16) & 255;
         const int Sw = S - A.J + 1, h = Sw >> 1, t0 = A.hmax - h;
@@ -497,9 +603,20 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
                 }
             }
             G[e] = out;
+            const float m = fabsf(out.x) + fabsf(out.y);
+            tmax = fmaxf(tmax, m);
+            tsum += m;
         }
+        // bounds for the fixed-point grid step: max |t.x| + |t.y| over all taps, max over
+        // visibilities of the tap sum (non-negative floats order like their bit patterns)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        if (lane == 0) atomicMax(A.fx + FX_T1, __float_as_uint(tsum));
         __syncwarp();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    if (lane == 0) atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
 }
 
 size_t gbuild_smem(int L, int hmax) {
@@ -528,6 +645,7 @@ void launch_gbuild(const rimo_plan* p, cudaStream_t s) {
     A.J = p->J;
     A.literal = p->prm.taper_literal != 0;
     A.nvis = p->M;
+    A.fx = p->d_fx;
     const size_t sm = gbuild_smem(p->L, p->hmax);
     RIMO_CUDA(cudaFuncSetAttribute(gbuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int dev = 0, nsm = 0;

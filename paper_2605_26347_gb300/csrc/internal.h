@@ -117,6 +117,7 @@ struct rimo_plan {
     int32_t* d_need_list = nullptr;  // per bin: the needed tiles as tu * ntv + tv
     int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)
     int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
+    uint32_t* d_fx = nullptr;      // fixed-point grid-step bounds (layout: rimo::FX_*)
     int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     float2* d_AB = nullptr;    // half-transformed intermediates (2 nx ny)
     float2* d_delta = nullptr; // delta image for the PSF
@@ -139,7 +140,25 @@ namespace rimo {
 void* dev_alloc(rimo_plan* p, size_t bytes);
 
 enum Stage { ST_FWD_ROWS = 0, ST_FWD_COLS = 1, ST_CLEAR = 2, ST_GTG = 3, ST_INV_COLS = 4,
-             ST_INV_ROWS = 5, ST_GBUILD = 6, ST_HBUILD = 7, ST_HAPPLY = 8, ST_MLP = 9 };
+             ST_INV_ROWS = 5, ST_GBUILD = 6, ST_HBUILD = 7, ST_HAPPLY = 8, ST_MLP = 9, ST_BOUND = 10 };
+
+// Fixed-point grid step.  The grid step accumulates each tile patch in two 32-bit integer
+// words per real number (hi: the contribution scaled by a power of two s and rounded;
+// lo: the rounding residual scaled by 2^16 more), so that the sums are exact integer sums
+// (independent of the order of the additions) of the FP32 contributions, to 2^-16 / s.
+// s is chosen per work unit from an a-priori bound on every contribution ("maxterm"),
+// and the number n of visibilities of the unit: |hi| <= n 2^21 s-scaled terms stay below
+// 2^31, |lo| <= n 2^15 likewise for n < 2^16.
+// d_fx layout (32-bit words):
+constexpr int FX_TMAX = 0;      // max over taps of |t.x| + |t.y| (float bits; plan time)
+constexpr int FX_T1 = 1;        // max over visibilities of sum over taps of |t.x| + |t.y|
+constexpr int FX_MAXTERM = 2;   // bound on |contribution| of the current apply (float)
+constexpr int FX_YMAX = 3;      // running max of |y.x| + |y.y| (float bits)
+constexpr int FX_COUNT = 4;     // blocks done (last-block reduction)
+constexpr int FX_PART = 64;     // per-block partial sums
+constexpr int FX_NPART = 1024;
+constexpr int FX_WORDS = FX_PART + FX_NPART;
+constexpr int FX_MAX_UNIT = 32768;  // visibilities per work unit (lo word range)
 // Bracket a group of `launches` kernel launches of one stage on stream s (no-op when off).
 void prof_begin(rimo_plan* p, int stage, cudaStream_t s);
 void prof_end(rimo_plan* p, int launches, cudaStream_t s);
@@ -157,5 +176,9 @@ void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, 
 void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,
                 cudaStream_t s);
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
+// bound on the grid-step contributions of Phi^dagger Phi x (from the image x) or of
+// Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
+void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);
+void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s);
 
 }  // namespace rimo

@@ -229,7 +229,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->gy = 2 * q.ny;
     p->J = q.kb_support;
     p->beta = q.kb_beta > 0 ? q.kb_beta : 2.34 * q.kb_support;
-    p->TS = q.tile_size ? q.tile_size : 64;
+    p->TS = q.tile_size ? q.tile_size : 32;
     p->M = M;
     planner::Params pr = planner_params(q);
     p->L = pr.kg.L;
@@ -327,6 +327,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         double r, bytes;
     };
     std::vector<std::vector<T>> tl(P);
+    std::vector<int32_t> tmp;
     double total_bytes = 0.0;
     for (int b = 0; b < P; ++b) {
         for (int64_t t = 0; t < ntile; ++t) {
@@ -341,6 +342,20 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
             if (cu >= gx / 2) cu -= gx;
             if (cv >= gy / 2) cv -= gy;
             x.r = std::sqrt(cu * cu + cv * cv);
+            // Interleave the tile's visibilities (arrival order within a tile is time, so
+            // neighbours are the same few baselines a fraction of a cell apart): viewed
+            // as 16 rows of nc, the new order reads the list column by column, so that
+            // any 16 consecutive visibilities - one ring chunk, de-gridded and gridded
+            // at the same time by 16 warps - come from 16 far-apart instants and rarely
+            // update the same grid cells.
+            {
+                const int64_t n = x.ve - x.vb, nc = (n + 15) / 16;
+                tmp.assign(order.begin() + x.vb, order.begin() + x.ve);
+                int64_t o = x.vb;
+                for (int64_t c = 0; c < nc; ++c)
+                    for (int64_t r = 0; r < 16; ++r)
+                        if (r * nc + c < n) order[o++] = tmp[r * nc + c];
+            }
             x.bytes = 0;
             for (int64_t i = x.vb; i < x.ve; ++i) {
                 int64_t S = sw[order[i]] + J - 1;
@@ -416,7 +431,8 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     }
     for (int b = 0; b < P; ++b) {
         const int64_t bin_vis = bstart[b + 1] - bstart[b];
-        const int64_t cap = std::max<int64_t>(256, (bin_vis + 2 * nsm_host - 1) / (2 * (int64_t)nsm_host));
+        const int64_t cap = std::min<int64_t>(
+            FX_MAX_UNIT, std::max<int64_t>(256, (bin_vis + 2 * nsm_host - 1) / (2 * (int64_t)nsm_host)));
         p->bins[b].t0 = (int32_t)p->tiles_host.size();
         p->bins[b].m0 = (int32_t)p->merge_host.size();
         for (const auto& x : tl[b]) {
@@ -512,6 +528,8 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
     p->d_status = (int32_t*)dev_alloc(p, sizeof(int32_t));
     RIMO_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s));
+    p->d_fx = (uint32_t*)dev_alloc(p, FX_WORDS * sizeof(uint32_t));
+    RIMO_CUDA(cudaMemsetAsync(p->d_fx, 0, FX_WORDS * sizeof(uint32_t), s));
     {
         int dev = 0;
         RIMO_CUDA(cudaGetDevice(&dev));

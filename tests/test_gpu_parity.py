@@ -106,8 +106,8 @@ def test_mono256_fused_equals_sequential_and_adjoint_identity(mono256):
     # J = 9 with a w-kernel cap of 5, literal taper, L = 32, tile size 32
     dict(nx=256, ny=128, fx=2.0, fy=2.0, m=3000,
          kw=dict(n_wbins=2, kb_support=9, max_wsupport=5, taper_literal=1, wkernel_L=32, tile_size=32)),
-    # automatic P, J = 3, energy fraction 0.99
-    dict(nx=128, ny=128, fx=3.0, fy=3.0, m=5000, kw=dict(kb_support=3, w_norm_frac=0.99)),
+    # automatic P, J = 3, energy fraction 0.99, tile size 64
+    dict(nx=128, ny=128, fx=3.0, fy=3.0, m=5000, kw=dict(kb_support=3, w_norm_frac=0.99, tile_size=64)),
 ])
 def test_ragged_and_edge_cases(case):
     uvw = synth.make_uvw(case["m"], 60, 1.28e9, 500 + case["m"])
@@ -142,3 +142,50 @@ def test_invalid_buffers_are_rejected(mono256):
     assert e.value.status == 1
     with pytest.raises(ValueError):
         plan.phi(torch.zeros((128, 256), dtype=torch.complex64, device="cuda"))
+
+
+def test_grid_step_sums_do_not_depend_on_timing(mono256):
+    # the grid step adds integers (fixed point), so repeated applies agree bit for bit
+    w, plan, _ = mono256
+    rng = np.random.default_rng(5)
+    y = (rng.standard_normal(w.uvw.shape[0]) + 1j * rng.standard_normal(w.uvw.shape[0])).astype(np.complex64)
+    xd, yd = to_dev(w.sky), to_dev(y)
+    a, b = to_host(plan.phi_adj_phi(xd)), to_host(plan.phi_adj_phi(xd))
+    assert np.array_equal(a, b)
+    a, b = to_host(plan.phi_adj(yd)), to_host(plan.phi_adj(yd))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-6, 1e6, 1e20])
+def test_grid_step_follows_input_magnitude(mono256, scale):
+    # the fixed-point scales come from bounds on the inputs: any magnitude keeps the accuracy
+    w, plan, op = mono256
+    rng = np.random.default_rng(6)
+    y = (rng.standard_normal(w.uvw.shape[0]) + 1j * rng.standard_normal(w.uvw.shape[0]))
+    ref_adj = op.phi_adj(y)
+    ref_ata = op.phi_adj_phi(w.sky.astype(np.complex128))
+    out_adj = to_host(plan.phi_adj(to_dev((y * scale).astype(np.complex64)))) / scale
+    out_ata = to_host(plan.phi_adj_phi(to_dev((w.sky * scale).astype(np.complex64)))) / scale
+    assert rel(out_adj, ref_adj) < TOL
+    assert rel(out_ata, ref_ata) < TOL
+
+
+def test_non_finite_input_is_reported(mono256):
+    import torch
+    import paper_2605_26347_gb300 as pkg
+    w, plan, _ = mono256
+    stream = torch.cuda.current_stream().cuda_stream
+    x = w.sky.copy()
+    x[17, 3] = np.nan
+    plan.phi_adj_phi(to_dev(x))
+    with pytest.raises(pkg.RimoError) as e:
+        pkg._lib.check(plan._lib.rimo_plan_status(plan._h, stream))
+    assert e.value.status == 1
+    y = np.ones(w.uvw.shape[0], dtype=np.complex64)
+    y[5] = np.inf
+    plan.phi_adj(to_dev(y))
+    with pytest.raises(pkg.RimoError):
+        pkg._lib.check(plan._lib.rimo_plan_status(plan._h, stream))
+    # the flag is cleared and finite inputs work again
+    plan.phi_adj_phi(to_dev(w.sky))
+    pkg._lib.check(plan._lib.rimo_plan_status(plan._h, stream))
