@@ -18,6 +18,9 @@
 // registers (16 points per thread, N/16 threads), exchanging through shared memory.
 #include <cstdio>
 
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 
 namespace rimo {
@@ -283,9 +286,30 @@ __global__ void __launch_bounds__(256) image_bound_kernel(const float2* __restri
     }
 }
 
+// ----------------------------------------------------------------------------- clusters
+// Transposed stores are made cluster-wide: the C CTAs of a thread-block cluster hold C x RB
+// consecutive rows (or columns) in their shared memory; after a cluster barrier each CTA
+// writes 1/C of the outputs for all C x RB of them, reading its partners' rows through
+// distributed shared memory, so that every global write is C x RB x 8 contiguous bytes
+// (64 bytes for C x RB = 8) instead of RB x 8.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t dsmem_map(const void* ptr, uint32_t rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(ptr);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 dsmem_ld2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+
 // ----------------------------------------------------------------------------- forward rows
 // grid: ny / RB blocks of RB * N/16 threads; block b transforms image rows [b RB, b RB + RB).
-template <int N, int RB>
+template <int N, int RB, int C>
 __global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At,
                                                                 int ny, ZArgs z, const float2* __restrict__ tw2N,
                                                                 const float2* __restrict__ tws) {
@@ -311,16 +335,37 @@ __global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (102
         fft_n<N, false>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
-        __syncthreads();
-        // transposed store: At[(2k + r) * ny + i0 + g'] for the RB rows, RB/2 float4 per k
-        const int i0 = blockIdx.x * RB;
-        for (int e = threadIdx.x; e < N * (RB / 2); e += blockDim.x) {
-            const int k = e / (RB / 2), gp = (e % (RB / 2)) * 2;
-            float2 a = smem[gp * (N + N / 16) + pidx(k)];
-            float2 b = smem[(gp + 1) * (N + N / 16) + pidx(k)];
-            *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + i0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+        if constexpr (C == 1) {
+            __syncthreads();
+            // transposed store: At[(2k + r) * ny + i0 + g'] for the RB rows, RB/2 float4 per k
+            const int i0 = blockIdx.x * RB;
+            for (int e = threadIdx.x; e < N * (RB / 2); e += blockDim.x) {
+                const int k = e / (RB / 2), gp = (e % (RB / 2)) * 2;
+                float2 a = smem[gp * (N + N / 16) + pidx(k)];
+                float2 b = smem[(gp + 1) * (N + N / 16) + pidx(k)];
+                *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + i0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            __syncthreads();
+        } else {
+            // cluster-wide transposed store: this CTA writes k in [rank N / C, (rank + 1) N / C)
+            // for the C x RB rows of the cluster; thread pair slot q (fixed per thread) holds
+            // rows 2q, 2q + 1 of the cluster, which live in CTA 2q / RB
+            cluster_sync_all();
+            constexpr int NP = C * RB / 2, KPC = N / C;
+            const int rank = (int)(blockIdx.x % C);
+            const int ibase = (int)(blockIdx.x - rank) * RB;
+            const int q = threadIdx.x % NP;
+            const int src = (2 * q) / RB, gp = (2 * q) % RB;
+            const uint32_t b0 = dsmem_map(smem + gp * (N + N / 16), src);
+            const uint32_t b1 = dsmem_map(smem + (gp + 1) * (N + N / 16), src);
+            for (int e = threadIdx.x; e < KPC * NP; e += blockDim.x) {
+                const int k = rank * KPC + e / NP;
+                const float2 a = dsmem_ld2(b0 + (uint32_t)pidx(k) * 8u);
+                const float2 b = dsmem_ld2(b1 + (uint32_t)pidx(k) * 8u);
+                *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + ibase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            cluster_sync_all();  // partners are done reading before the rows are reused
         }
-        __syncthreads();
     }
 }
 
@@ -402,7 +447,7 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs F) {
 // grid: gx / RB blocks; rows u of Xh (2N cells along v; cells of tiles without a mark in
 // need[] are zero and not read) -> B[i][u] for the N image rows.  The RB rows of a block
 // lie in one tile row (RB <= TS).
-template <int N, int RB>
+template <int N, int RB, int C>
 __global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B,
                                                                 int gx, const uint8_t* __restrict__ need, int shift,
                                                                 const float2* __restrict__ tw2N,
@@ -433,19 +478,42 @@ __global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv
         fft_n<N, true>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
-        __syncthreads();
         // keep outputs m' in [0, N/4) u [3N/4, N): image row i = 2 mm + r + N/2
-        const int u0 = blockIdx.x * RB;
-        for (int e = threadIdx.x; e < (N / 2) * (RB / 2); e += blockDim.x) {
-            const int kk = e / (RB / 2), gp = (e % (RB / 2)) * 2;
-            const int mp = kk < N / 4 ? kk : kk + N / 2;
-            const int mm = kk < N / 4 ? kk : kk - N / 2;
-            const int i = 2 * mm + r + N / 2;
-            float2 a = smem[gp * (N + N / 16) + pidx(mp)];
-            float2 b = smem[(gp + 1) * (N + N / 16) + pidx(mp)];
-            *reinterpret_cast<float4*>(&B[(size_t)i * gx + u0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+        if constexpr (C == 1) {
+            __syncthreads();
+            const int u0 = blockIdx.x * RB;
+            for (int e = threadIdx.x; e < (N / 2) * (RB / 2); e += blockDim.x) {
+                const int kk = e / (RB / 2), gp = (e % (RB / 2)) * 2;
+                const int mp = kk < N / 4 ? kk : kk + N / 2;
+                const int mm = kk < N / 4 ? kk : kk - N / 2;
+                const int i = 2 * mm + r + N / 2;
+                float2 a = smem[gp * (N + N / 16) + pidx(mp)];
+                float2 b = smem[(gp + 1) * (N + N / 16) + pidx(mp)];
+                *reinterpret_cast<float4*>(&B[(size_t)i * gx + u0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            __syncthreads();
+        } else {
+            // cluster-wide transposed store (see fwd_rows_kernel): this CTA writes outputs kk in
+            // [rank N / (2C), (rank + 1) N / (2C)) for the C x RB grid rows u of the cluster
+            cluster_sync_all();
+            constexpr int NP = C * RB / 2, KPC = (N / 2) / C;
+            const int rank = (int)(blockIdx.x % C);
+            const int ubase = (int)(blockIdx.x - rank) * RB;
+            const int q = threadIdx.x % NP;
+            const int src = (2 * q) / RB, gp = (2 * q) % RB;
+            const uint32_t b0 = dsmem_map(smem + gp * (N + N / 16), src);
+            const uint32_t b1 = dsmem_map(smem + (gp + 1) * (N + N / 16), src);
+            for (int e = threadIdx.x; e < KPC * NP; e += blockDim.x) {
+                const int kk = rank * KPC + e / NP;
+                const int mp = kk < N / 4 ? kk : kk + N / 2;
+                const int mm = kk < N / 4 ? kk : kk - N / 2;
+                const int i = 2 * mm + r + N / 2;
+                const float2 a = dsmem_ld2(b0 + (uint32_t)pidx(mp) * 8u);
+                const float2 b = dsmem_ld2(b1 + (uint32_t)pidx(mp) * 8u);
+                *reinterpret_cast<float4*>(&B[(size_t)i * gx + ubase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            cluster_sync_all();
         }
-        __syncthreads();
     }
 }
 
@@ -519,13 +587,40 @@ template <int N>
 static constexpr int inv_rows_per_block() { return (N / 16) >= 256 ? 2 : rows_per_block<N>(); }
 template <int N>
 static constexpr int groups_per_block() { return (N / 16) >= 256 ? 1 : 256 / (N / 16); }
+// CTAs per cluster of the transposed-store passes: 8 rows per cluster (64-byte writes)
+template <int RB>
+static constexpr int cluster_of() { return RB >= 8 ? 1 : 8 / RB; }
 
+template <class... KArgs, class... Args>
+static void launch_clustered(void (*kernel)(KArgs...), int grid, int block, size_t smem, int C, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    RIMO_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+}
+
+// Raises a kernel's dynamic shared-memory limit once per (device, kernel, size).
 template <class K>
 static void set_smem(K kernel, size_t bytes) {
-    static bool done = false;  // per template instance
-    if (!done) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    RIMO_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{dev, reinterpret_cast<const void*>(kernel)}];
+    if (have < bytes) {
         RIMO_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        done = true;
+        have = bytes;
     }
 }
 
@@ -544,9 +639,17 @@ static void set_smem(K kernel, size_t bytes) {
 template <int N>
 static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
     constexpr int RB = rows_per_block<N>();
+    constexpr int C = cluster_of<RB>();
     const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
-    set_smem(fwd_rows_kernel<N, RB>, sm);
-    fwd_rows_kernel<N, RB><<<p->ny / RB, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x, p->tab.tws_x);
+    const int grid = p->ny / RB;
+    if (C > 1 && grid % C == 0) {
+        set_smem(fwd_rows_kernel<N, RB, C>, sm);
+        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 16, sm, C, s, x, At, p->ny, zargs(p, bin),
+                         (const float2*)p->tab.tw_x, (const float2*)p->tab.tws_x);
+    } else {
+        set_smem(fwd_rows_kernel<N, RB, 1>, sm);
+        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x, p->tab.tws_x);
+    }
 }
 
 template <int N>
@@ -562,8 +665,8 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     constexpr int RB = inv_rows_per_block<N>();
+    constexpr int C = cluster_of<RB>();
     const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 256;
-    set_smem(inv_cols_kernel<N, RB>, sm);
     const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
     const size_t ntile = (size_t)ntu * ntv;
     const auto& br = p->bins[bin];
@@ -581,8 +684,17 @@ static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
         F.gy = p->gy;
         fold_kernel<<<br.n1 - br.n0, 256, 0, s>>>(F);
     }
-    inv_cols_kernel<N, RB><<<p->gx / RB, RB * N / 16, sm, s>>>(p->d_X, B, p->gx, p->d_need + (size_t)bin * ntile,
-                                                                p->TS == 64 ? 6 : 5, p->tab.tw_y, p->tab.tws_y);
+    const int grid = p->gx / RB, shift = p->TS == 64 ? 6 : 5;
+    const uint8_t* need = p->d_need + (size_t)bin * ntile;
+    if (C > 1 && grid % C == 0) {
+        set_smem(inv_cols_kernel<N, RB, C>, sm);
+        launch_clustered(inv_cols_kernel<N, RB, C>, grid, RB * N / 16, sm, C, s, (const float2*)p->d_X, B, p->gx,
+                         need, shift, (const float2*)p->tab.tw_y, (const float2*)p->tab.tws_y);
+    } else {
+        set_smem(inv_cols_kernel<N, RB, 1>, sm);
+        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 16, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tw_y,
+                                                                p->tab.tws_y);
+    }
 }
 
 template <int N>

@@ -189,3 +189,18 @@ def test_non_finite_input_is_reported(mono256):
     # the flag is cleared and finite inputs work again
     plan.phi_adj_phi(to_dev(w.sky))
     pkg._lib.check(plan._lib.rimo_plan_status(plan._h, stream))
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_large_image_parity(n):
+    # image sizes whose transposed-store passes run as thread-block clusters (2 and 4 CTAs)
+    uvw = synth.make_uvw(20000, 28_800, 1.28e9, 700 + n)
+    fov = math.radians(3.0)
+    plan, op = both(uvw, n, n, fov, fov, n_wbins=2)
+    assert_same_plan(plan, op)
+    x = synth.make_sky(n, 800 + n)
+    rng = np.random.default_rng(n)
+    y = (rng.standard_normal(20000) + 1j * rng.standard_normal(20000)).astype(np.complex64)
+    assert rel(to_host(plan.phi(to_dev(x))), op.phi(x.astype(np.complex128))) < TOL
+    assert rel(to_host(plan.phi_adj(to_dev(y))), op.phi_adj(y.astype(np.complex128))) < TOL
+    assert rel(to_host(plan.phi_adj_phi(to_dev(x))), op.phi_adj_phi(x.astype(np.complex128))) < TOL
