@@ -131,6 +131,9 @@ typedef struct rimo_plan_info {
     double wr_max;             /* max |w - w_stack[bin]|                           */
     double wsclean_p;          /* Eq. 5 bound                                      */
     int32_t support_table[64]; /* S_w per uniform |w_r| bin                        */
+    int32_t tile_size;         /* uv-tile edge of the gridding schedule (0: none)  */
+    int32_t truncated;         /* 1: at the largest residual w the kernel needs more */
+                               /* than max_wsupport taps to keep w_norm_frac         */
 } rimo_plan_info;
 
 typedef struct rimo_plan* rimo_plan_t;
@@ -315,6 +318,49 @@ rimo_status rimo_surrogate_gradients(rimo_surrogate_t s, const float* x_dev, con
  * NULL, then no synchronisation) receives the batch loss before the step. */
 rimo_status rimo_surrogate_train_step(rimo_surrogate_t s, const float* x_dev, const float* t_dev,
                                       int64_t B, float lr, float* loss, void* stream);
+
+/*
+ * Batched wideband Phi^dagger Phi.  The wideband model applies the monochromatic operator
+ * per frequency channel (Section 2; per-frequency worker pools, Section 3.5): a batch
+ * groups independent plans, one per channel, each with its own uvw, w-stack and sizes of
+ * w-bins, and all of the same image size.  The caller keeps owning the plans (destroy the
+ * batch first); a plan may belong to one batch at a time and must not be applied on its
+ * own while a batch call using it is in flight (plans have scratch).
+ */
+typedef struct rimo_batch* rimo_batch_t;
+/* Errors: INVALID_ARG (no plans, NULL plan, a plan twice, image sizes differ, plans on
+ * another device), CUDA. */
+rimo_status rimo_batch_create(const rimo_plan_t* plans, int32_t n_plans, rimo_batch_t* out);
+/* NULL is accepted. */
+rimo_status rimo_batch_destroy(rimo_batch_t batch);
+/*
+ * out[c] = Phi_c^dagger Phi_c x[c] for every channel c of the batch, where x_dev and
+ * out_dev hold n_plans images of ny x nx complex64 back to back (device, distinct,
+ * non-overlapping).  The first call, and any call with other buffers or another
+ * real_part_only, records every channel's apply into one CUDA graph (each channel on its
+ * own forked branch of `stream`, so channels run concurrently); each call then enqueues
+ * that graph with a single launch on `stream`.  Per-plan stage timers are not recorded
+ * inside the graph.  Device-side error flags are per plan (rimo_plan_status).
+ * Errors: INVALID_ARG, CUDA.
+ */
+rimo_status rimo_batch_apply_phi_adj_phi(rimo_batch_t batch, const rimo_cfloat* x_dev, rimo_cfloat* out_dev,
+                                         int32_t real_part_only, void* stream);
+/* Number of plans and how many times the graph was recorded (either may be NULL). */
+rimo_status rimo_batch_info(rimo_batch_t batch, int32_t* n_plans, int64_t* captures);
+
+/*
+ * Tile-size autotuner (no counterpart in the paper: a scheduling choice of this design).
+ * Times Phi^dagger Phi with uv-tile sizes 32 and 64 on plans built from a deterministic
+ * subsample of uvw (every ceil(M / 2^20)-th row) with the other fields of `base`, and
+ * writes the faster one to *tile_out.  cache_path (host string, may be NULL or ""): a JSON
+ * object {"key": tile, ...} keyed by image size, FoV, log2 M, P, J and maximum tile side;
+ * a hit returns without timing, a miss adds the result (the file is rewritten whole).
+ * ms_out (host, 2 values, may be NULL): the measured ms per apply for 32 and 64, or -1
+ * when not timed.  Allocates and frees two image buffers and two plans; synchronises
+ * `stream`.  Errors: INVALID_ARG (also for an unwritable cache), OOM, BUDGET, CUDA.
+ */
+rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
+                               void* stream, int32_t* tile_out, double* ms_out);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rimo_last_error(void);

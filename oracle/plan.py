@@ -165,7 +165,10 @@ def model_for_P(w_sub: np.ndarray, M: int, P: int, pp: PlanParams) -> dict:
     m_G = 8.0 * KP + META_BYTES_PER_VIS * M
     Np = (pp.oversampling ** 2) * pp.nx * pp.ny
     cost = 2.0 * (10.0 * Np * math.log2(math.sqrt(Np)) * P + 6.0 * K)
-    return dict(P=P, K=K, m_G=m_G, cost=cost)
+    wr_max = float(np.max(np.abs(w_r))) if w_r.size else 0.0
+    trunc = wterm.truncated_at(wr_max, pp.L, pp.fov_x, pp.fov_y, pp.w_norm_frac, pp.max_wsupport,
+                               pp.taper_literal)
+    return dict(P=P, K=K, m_G=m_G, cost=cost, truncated=trunc)
 
 
 def choose(uvw: np.ndarray, pp: PlanParams) -> dict:
@@ -181,7 +184,14 @@ def choose(uvw: np.ndarray, pp: PlanParams) -> dict:
         cands = [p for p in CANDIDATE_P if p <= max(pmax, 1)]
         cands = [p for p in cands if p <= max(1, w_sub.shape[0])]
     models = [model_for_P(w_sub, M, p, pp) for p in cands]
-    best = min(models, key=lambda d: (d["cost"], d["P"]))
+    # With an automatic P, only bin counts whose residual kernels fit the support cap keep
+    # the eta norm fraction of Section 3.1; if none does, the largest candidate truncates
+    # least.  (A capped support makes K(P) flat in P, so the cost model alone would pick
+    # the fewest bins however much of the kernels the cap cuts off.)
+    pool = [d for d in models if not d["truncated"]] if pp.n_wbins == 0 else models
+    if not pool:
+        pool = [max(models, key=lambda d: d["P"])]
+    best = min(pool, key=lambda d: (d["cost"], d["P"]))
     budget = pp.mem_budget_bytes
     out = dict(models=models, p_star=best["P"], subset=int(w_sub.shape[0]))
     if pp.mode != MODE_AUTO:
@@ -190,7 +200,8 @@ def choose(uvw: np.ndarray, pp: PlanParams) -> dict:
     if budget <= 0 or best["m_G"] <= budget:
         out.update(P=best["P"], mode=MODE_STORED_G)
         return out
-    feas = [d for d in models if d["m_G"] <= budget]
+    # under the budget: the nearest P to P* that fits, kernels within the cap preferred
+    feas = [d for d in pool if d["m_G"] <= budget] or [d for d in models if d["m_G"] <= budget]
     if feas:
         pick = min(feas, key=lambda d: (abs(d["P"] - best["P"]), d["P"]))
         out.update(P=pick["P"], mode=MODE_STORED_G)

@@ -121,6 +121,20 @@ def support_of(K_full: np.ndarray, eta: float, max_wsupport: int) -> int:
     return max_wsupport
 
 
+def truncated_at(w_r: float, L: int, fov_x: float, fov_y: float, eta: float,
+                 max_wsupport: int, literal: bool = False) -> bool:
+    """Whether the kernel of residual w_r needs more than max_wsupport taps per axis to keep
+    eta of its l2 norm (then the capped support truncates it, Section 3.1)."""
+    if w_r == 0.0 or eta >= 1.0:
+        return False
+    K = wkernel_full(w_r, L, fov_x, fov_y, literal)
+    c = L // 2
+    h = max_wsupport // 2
+    total = math.sqrt(float(np.sum(np.abs(K) ** 2)))
+    blk = K[c - h:c + h + 1, c - h:c + h + 1]
+    return math.sqrt(float(np.sum(np.abs(blk) ** 2))) < eta * total
+
+
 def support_table(wr_max: float, L: int, fov_x: float, fov_y: float, eta: float,
                   max_wsupport: int, literal: bool = False) -> np.ndarray:
     """Support S_w for each of 64 uniform |w_r| bins over [0, wr_max], non-decreasing."""

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (MODE_AUTO, MODE_HOLOGRAPHIC, MODE_ONTHEFLY, MODE_STORED_G, MODE_SURROGATE,
                    PlanInfo, PlanParams, RimoError)
 
-__all__ = ["Plan", "PlanParams", "PlanInfo", "RimoError", "default_params", "estimate",
+__all__ = ["Plan", "PlanParams", "PlanInfo", "RimoError", "default_params", "estimate", "Batch", "autotune_tile",
            "MODE_AUTO", "MODE_STORED_G", "MODE_HOLOGRAPHIC", "MODE_SURROGATE", "MODE_ONTHEFLY"]
 
 
@@ -234,6 +234,67 @@ class Surrogate:
                                                        float(lr), C.byref(loss) if want_loss else None,
                                                        _stream_ptr(stream)))
         return float(loss.value) if want_loss else None
+
+
+class Batch:
+    """Batched wideband Phi^dagger Phi over per-channel plans (rimo_batch_create).
+
+    Keeps references to the plans; they must outlive the batch and share one image size.
+    """
+
+    def __init__(self, plans):
+        self._lib = _lib.load()
+        self.plans = list(plans)
+        if not self.plans:
+            raise ValueError("a batch needs at least one plan")
+        self.nx, self.ny = self.plans[0].nx, self.plans[0].ny
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = C.c_void_p()
+        _lib.check(self._lib.rimo_batch_create(arr, len(self.plans), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rimo_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def phi_adj_phi(self, x, out=None, real_part_only=False, stream=None):
+        """x, out: contiguous complex64 CUDA tensors of shape (n_plans, ny, nx)."""
+        torch = _torch()
+        shape = (len(self.plans), self.ny, self.nx)
+        if not (x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous() and tuple(x.shape) == shape):
+            raise ValueError(f"x must be a contiguous complex64 CUDA tensor of shape {shape}")
+        if out is None:
+            out = torch.empty_like(x)
+        elif not (out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous() and tuple(out.shape) == shape):
+            raise ValueError(f"out must be a contiguous complex64 CUDA tensor of shape {shape}")
+        _lib.check(self._lib.rimo_batch_apply_phi_adj_phi(self._h, x.data_ptr(), out.data_ptr(),
+                                                          int(real_part_only), _stream_ptr(stream)))
+        return out
+
+    def info(self) -> dict:
+        n = C.c_int32()
+        caps = C.c_int64()
+        _lib.check(self._lib.rimo_batch_info(self._h, C.byref(n), C.byref(caps)))
+        return {"n_plans": n.value, "captures": caps.value}
+
+
+def autotune_tile(uvw, params: PlanParams, cache_path: str | None = None, stream=None) -> tuple[int, list]:
+    """rimo_autotune_tile: (best uv-tile size, [ms at 32, ms at 64] or -1 where not timed)."""
+    lib = _lib.load()
+    u = _uvw_arg(uvw)
+    tile = C.c_int32()
+    ms = (C.c_double * 2)()
+    path = cache_path.encode() if cache_path else None
+    _lib.check(lib.rimo_autotune_tile(u.ctypes.data, u.shape[0], C.byref(params), path, _stream_ptr(stream),
+                                      C.byref(tile), ms))
+    return tile.value, [ms[0], ms[1]]
 
 
 def unpack_params(p: np.ndarray) -> dict:

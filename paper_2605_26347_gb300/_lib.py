@@ -64,6 +64,8 @@ class PlanInfo(C.Structure):
         ("wr_max", C.c_double),
         ("wsclean_p", C.c_double),
         ("support_table", C.c_int32 * 64),
+        ("tile_size", C.c_int32),
+        ("truncated", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -97,6 +99,11 @@ _PROTOS = {
     "rimo_surrogate_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "rimo_surrogate_gradients": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "rimo_surrogate_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
+    "rimo_batch_create": (C.c_int, [_P, C.c_int32, C.POINTER(_P)]),
+    "rimo_batch_destroy": (C.c_int, [_P]),
+    "rimo_batch_apply_phi_adj_phi": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
+    "rimo_batch_info": (C.c_int, [_P, _P, _P]),
+    "rimo_autotune_tile": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

@@ -135,18 +135,6 @@ void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only
 
 using namespace rimo;
 
-#define RIMO_API_BEGIN try {
-#define RIMO_API_END                  \
-    return RIMO_OK;                   \
-    }                                 \
-    catch (const Error& e) {          \
-        set_last_error(e.msg);        \
-        return e.status;              \
-    }                                 \
-    catch (const std::exception& e) { \
-        set_last_error(e.what());     \
-        return RIMO_ERR_OOM;          \
-    }
 
 extern "C" {
 

@@ -18,6 +18,20 @@ struct Error {
     std::string msg;
 };
 void set_last_error(const std::string& msg);
+
+// Body of a C-ABI entry point: errors become status codes and rimo_last_error().
+#define RIMO_API_BEGIN try {
+#define RIMO_API_END                  \
+    return RIMO_OK;                   \
+    }                                 \
+    catch (const Error& e) {          \
+        set_last_error(e.msg);        \
+        return e.status;              \
+    }                                 \
+    catch (const std::exception& e) { \
+        set_last_error(e.what());     \
+        return RIMO_ERR_OOM;          \
+    }
 [[noreturn]] void fail(rimo_status s, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 #define RIMO_CUDA(call) ::rimo::check_cuda((call), #call)
@@ -119,6 +133,7 @@ struct rimo_plan {
     int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
     uint32_t* d_fx = nullptr;      // fixed-point grid-step bounds (layout: rimo::FX_*)
     int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
+    int device = 0;                // CUDA device the plan lives on
     float2* d_AB = nullptr;    // half-transformed intermediates (2 nx ny)
     float2* d_delta = nullptr; // delta image for the PSF
     rimo::DevTables tab;
@@ -176,6 +191,11 @@ void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, 
 void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,
                 cudaStream_t s);
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
+
+// The three applies on stream s (defined in apply.cu).
+void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s);
+void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s);
+void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s);
 // bound on the grid-step contributions of Phi^dagger Phi x (from the image x) or of
 // Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);

@@ -40,7 +40,6 @@ static unsigned char* noalloc_scratch() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s);
 
 }  // namespace rimo
 

@@ -123,6 +123,8 @@ static void fill_estimate(rimo_plan_info* info, const planner::Choice& ch, int64
     info->est_cost = ch.est_cost;
     info->wsclean_p = ch.wsclean;
     info->wkernel_L = L;
+    for (const auto& m : ch.models)
+        if (m.P == ch.P) info->truncated = m.truncated ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -230,6 +232,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->J = q.kb_support;
     p->beta = q.kb_beta > 0 ? q.kb_beta : 2.34 * q.kb_support;
     p->TS = q.tile_size ? q.tile_size : 32;
+    p->info.tile_size = p->TS;
     p->M = M;
     planner::Params pr = planner_params(q);
     p->L = pr.kg.L;
@@ -257,6 +260,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     }
     std::vector<int32_t> tab = planner::support_table(wr_max, pr.kg);
     p->info.wr_max = wr_max;
+    p->info.truncated = planner::truncated_at(wr_max, pr.kg) ? 1 : 0;
     for (int i = 0; i < 64; ++i) p->info.support_table[i] = tab[i];
 
     // ---- placement on the oversampled grid: u~ = u * (2 fov_x), one FP64 multiply
@@ -534,6 +538,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         int dev = 0;
         RIMO_CUDA(cudaGetDevice(&dev));
         RIMO_CUDA(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
+        p->device = dev;
         const int s2 = p->max_S * p->max_S;
         p->chunk_vis = 16;
         p->chunk_bytes = p->chunk_vis * (s2 + (s2 & 1)) * (int)sizeof(float2);

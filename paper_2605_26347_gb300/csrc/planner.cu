@@ -147,9 +147,10 @@ static double taper(double lam, double fov) {
     return 0.54 + 0.46 * std::cos(M_PI * (a - half) / half);
 }
 
-// Support of the residual kernel at offset w_r: smallest odd s whose centred s x s taps
-// keep >= eta of the l2 norm of all L x L taps (norm by Parseval from the samples).
-int support_at(double w_r, const KernelGeom& g) {
+// Support of the residual kernel at offset w_r: smallest odd s <= max_wsupport whose
+// centred s x s taps keep >= eta of the l2 norm of all L x L taps (norm by Parseval from
+// the samples), or max_wsupport + 2 when even the cap keeps less (the cap truncates).
+static int support_raw(double w_r, const KernelGeom& g) {
     int L = g.L, hm = g.max_wsupport / 2, ns = 2 * hm + 1;
     std::vector<std::complex<double>> c((size_t)L * L);
     double tot = 0.0;
@@ -194,7 +195,14 @@ int support_at(double w_r, const KernelGeom& g) {
             for (int y = hm - h; y <= hm + h; ++y) e += std::norm(K[(size_t)x * ns + y]);
         if (std::sqrt(e) >= g.eta * total) return s;
     }
-    return g.max_wsupport;
+    return g.max_wsupport + 2;
+}
+
+int support_at(double w_r, const KernelGeom& g) { return std::min(support_raw(w_r, g), g.max_wsupport); }
+
+bool truncated_at(double w_r, const KernelGeom& g) {
+    if (w_r == 0.0 || g.eta >= 1.0) return false;
+    return support_raw(w_r, g) > g.max_wsupport;
 }
 
 std::vector<int32_t> support_table(double wr_max, const KernelGeom& g) {
@@ -244,6 +252,7 @@ static ModelPoint model_for_P(const std::vector<double>& w_sub, int64_t M, int P
     mp.m_G = 8.0 * KP + (double)META_BYTES_PER_VIS * (double)M;
     double Np = 4.0 * (double)pr.nx * (double)pr.ny;
     mp.cost = 2.0 * (10.0 * Np * std::log2(std::sqrt(Np)) * (double)P + 6.0 * mp.K);
+    mp.truncated = truncated_at(wr_max, pr.kg);
     return mp;
 }
 
@@ -261,9 +270,22 @@ Choice choose(const double* uvw, int64_t M, const Params& pr) {
             if (p <= std::max(pmax, 1) && p <= std::max<int64_t>(1, ch.subset)) cands.push_back(p);
     }
     for (int p : cands) ch.models.push_back(model_for_P(w_sub, M, p, pr));
-    const ModelPoint* best = &ch.models[0];
+    // With an automatic P only bin counts whose residual kernels fit the support cap keep
+    // the eta norm fraction (Section 3.1); if none does, the largest candidate truncates
+    // least.  A capped support makes K(P) flat in P, so cost alone would pick the fewest
+    // bins however much of the kernels the cap cuts off.
+    std::vector<const ModelPoint*> pool;
     for (const auto& m : ch.models)
-        if (m.cost < best->cost || (m.cost == best->cost && m.P < best->P)) best = &m;
+        if (pr.n_wbins > 0 || !m.truncated) pool.push_back(&m);
+    if (pool.empty()) {
+        const ModelPoint* mx = &ch.models[0];
+        for (const auto& m : ch.models)
+            if (m.P > mx->P) mx = &m;
+        pool.push_back(mx);
+    }
+    const ModelPoint* best = pool[0];
+    for (const ModelPoint* m : pool)
+        if (m->cost < best->cost || (m->cost == best->cost && m->P < best->P)) best = m;
     ch.p_star = best->P;
     ch.est_m_g = best->m_G;
     ch.est_cost = best->cost;
@@ -278,12 +300,18 @@ Choice choose(const double* uvw, int64_t M, const Params& pr) {
         ch.mode = RIMO_MODE_STORED_G;
         return ch;
     }
+    // under the budget: the nearest P to P* that fits, kernels within the cap preferred
     const ModelPoint* pick = nullptr;
-    for (const auto& m : ch.models) {
-        if (m.m_G > budget) continue;
-        if (!pick) { pick = &m; continue; }
-        int d = std::abs(m.P - best->P), dp = std::abs(pick->P - best->P);
-        if (d < dp || (d == dp && m.P < pick->P)) pick = &m;
+    std::vector<const ModelPoint*> all;
+    for (const auto& m : ch.models) all.push_back(&m);
+    for (const auto* set : {&pool, &all}) {
+        for (const ModelPoint* m : *set) {
+            if (m->m_G > budget) continue;
+            if (!pick) { pick = m; continue; }
+            int d = std::abs(m->P - best->P), dp = std::abs(pick->P - best->P);
+            if (d < dp || (d == dp && m->P < pick->P)) pick = m;
+        }
+        if (pick) break;
     }
     if (pick) {
         ch.P = pick->P;

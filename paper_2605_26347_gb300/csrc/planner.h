@@ -35,6 +35,7 @@ struct Params {
 struct ModelPoint {
     int P = 0;
     double K = 0, m_G = 0, cost = 0;
+    bool truncated = false;  // the support cap cuts the kernel at the largest residual w
 };
 
 struct Choice {
@@ -56,6 +57,7 @@ std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter);
 double dn(double l, double m);
 double wsclean_bound(const double* uvw, int64_t M, double fov_x, double fov_y);
 int support_at(double w_r, const KernelGeom& g);
+bool truncated_at(double w_r, const KernelGeom& g);
 std::vector<int32_t> support_table(double wr_max, const KernelGeom& g);
 int support_bin(double abs_wr, double wr_max);
 Choice choose(const double* uvw, int64_t M, const Params& pr);

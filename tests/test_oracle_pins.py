@@ -271,13 +271,18 @@ def test_decision_tree_regimes():
     base = dict(nx=256, ny=256, fov_x=math.radians(1.0), fov_y=math.radians(1.0))
     big = pl.choose(uvw, pl.PlanParams(**base))
     assert big["mode"] == pl.MODE_STORED_G and big["P"] == big["p_star"]
-    costs = {d["P"]: d["cost"] for d in big["models"]}
+    # the cost minimiser over the bin counts whose kernels fit the support cap
+    ok = [d for d in big["models"] if not d["truncated"]] or [max(big["models"], key=lambda d: d["P"])]
+    costs = {d["P"]: d["cost"] for d in ok}
     assert costs[big["P"]] == min(costs.values())
     mG = {d["P"]: d["m_G"] for d in big["models"]}
     mid_budget = int(0.5 * (mG[big["P"]] + min(mG.values())))
     mid = pl.choose(uvw, pl.PlanParams(**base, mem_budget_bytes=mid_budget))
     if mG[big["P"]] > mid_budget:
-        assert mid["mode"] == pl.MODE_STORED_G and mG[mid["P"]] <= mid_budget
+        if any(m <= mid_budget for m in mG.values()):
+            assert mid["mode"] == pl.MODE_STORED_G and mG[mid["P"]] <= mid_budget
+        else:
+            assert mid["mode"] == pl.MODE_HOLOGRAPHIC
     tiny = pl.choose(uvw, pl.PlanParams(**base, mem_budget_bytes=1000))
     assert tiny["mode"] == pl.MODE_HOLOGRAPHIC and tiny.get("check_h")
 
@@ -338,3 +343,34 @@ def test_gelu_gradient_matches_difference_quotient():
     h = 1e-6
     fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
     assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
+
+
+@pytest.mark.parametrize("fov_deg", [1.0, 2.5])
+def test_truncation_follows_chirp_bandwidth(fov_deg):
+    # The residual chirp e^{-2 pi i w_r (n - 1)} has local frequency -w_r l / n over the
+    # field, a spread of about w_r FoV cycles per unit l, i.e. 2 w_r FoV^2 grid cells
+    # (cell = 1 / (2 FoV)).  Far below one cell the 9-tap cap keeps the 0.9999 norm
+    # fraction; far above nine cells it cannot.
+    fov = math.radians(fov_deg)
+    L = wterm.wkernel_L(9)
+    for cells in (0.05, 0.25, 0.5):
+        assert not wterm.truncated_at(cells / (2 * fov * fov), L, fov, fov, 0.9999, 9)
+    for cells in (12.0, 40.0):
+        assert wterm.truncated_at(cells / (2 * fov * fov), L, fov, fov, 0.9999, 9)
+    assert not wterm.truncated_at(0.0, L, fov, fov, 0.9999, 9)
+
+
+def test_automatic_bins_avoid_truncated_kernels():
+    # auto P: the chosen bin count keeps every kernel within the cap whenever some
+    # candidate does, and any cheaper candidate is one whose kernels the cap truncates
+    uvw = synth.make_uvw(20000, 600, 1.28e9, 23)
+    pp = pl.PlanParams(nx=256, ny=256, fov_x=math.radians(2.5), fov_y=math.radians(2.5))
+    ch = pl.choose(uvw, pp)
+    by_p = {d["P"]: d for d in ch["models"]}
+    if any(not d["truncated"] for d in ch["models"]):
+        assert not by_p[ch["P"]]["truncated"]
+        for d in ch["models"]:
+            if d["cost"] < by_p[ch["P"]]["cost"]:
+                assert d["truncated"]
+    else:
+        assert ch["P"] == max(by_p)
