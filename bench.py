@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error sample and CPU baseline")
     ap.add_argument("--cpu-sample-vis", type=int, default=20000)
     ap.add_argument("--tile", type=int, default=0, help="uv-tile size (0: library default)")
-    ap.add_argument("--config", default="c5", choices=["c5", "wideband"],
+    ap.add_argument("--config", default="c5", choices=["c5", "wideband", "holo", "holo-dense"],
                     help="c5: the 4096^2 / 50M workload (default); wideband: 32 channels of 1024^2 "
-                         "batched into one graph launch")
+                         "batched into one graph launch; holo: 2048^2 / 20M / 16 bins with H_p = G_p^dagger G_p; "
+                         "holo-dense: 256^2 / 20M / 4 bins, where visibilities per grid cell are many")
     ap.add_argument("--channels", type=int, default=32, help="wideband: channels")
     ap.add_argument("--autotune", default="", help="wideband: JSON cache path; tile sizes by the autotuner")
     ap.add_argument("--wideband-bins", default="linear", choices=["linear", "auto"],
@@ -468,12 +469,84 @@ def run_wideband(args):
     print(json.dumps(line), flush=True)
 
 
+def run_holo(args):
+    """Phi^dagger Phi through the holographic matrices H_p against the G^dagger G path on the
+    same plan: build time, bytes, applies/s of both, and their relative l2 difference."""
+    import torch
+    import synth
+    import paper_2605_26347_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dense = args.config == "holo-dense"
+    n, fov, bins, m = (256, 1.0, 4, 20_000_000) if dense else (2048, 2.5, 16, 20_000_000)
+    if args.m != 50_000_000:
+        m = args.m
+    uvw = synth.make_uvw(m, 28_800, 1.28e9, seed=1003)
+    sky = synth.make_sky(n, seed=2003)
+    fovr = math.radians(fov)
+    t0 = time.time()
+    plan = pkg.Plan(uvw, pkg.default_params(n, n, fovr, fovr, n_wbins=bins, mode=pkg.MODE_STORED_G))
+    t_plan = time.time() - t0
+    x = torch.from_numpy(sky).cuda()
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(k):
+        for _ in range(args.warmup):
+            plan.phi_adj_phi(x, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        plan.profile(True)
+        plan.profile_read(reset=True)
+        e0.record(stream)
+        for _ in range(k):
+            plan.phi_adj_phi(x, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = plan.profile_read(reset=True)
+        plan.profile(False)
+        return e0.elapsed_time(e1) / k, {kk: v[0] / k for kk, v in prof.items() if v[1] > 0}
+
+    ms_g, st_g = timed(args.steps)
+    ref = out.clone()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    plan.build_holographic()
+    t_build = time.time() - t0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_h, st_h = timed(args.steps)
+    clk = clocks.stop()
+    diff = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+    info = plan.info()
+    if rank != 0:
+        return
+    line = {
+        "metric": "Phi^dagger Phi applies/s through H_p (G^dagger G path alongside)",
+        "value": ws * 1000.0 / ms_h, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_h, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": ("holographic dense: 256^2 image, FoV 1 deg, 20M visibilities, 4 w-bins" if dense
+                                else "holographic: 2048^2 image, 4096^2 grid, FoV 2.5 deg, 20M visibilities, 16 w-bins"),
+                   "n": n, "M": m, "P": info["P"], "parallelism": f"replicas x{ws}"},
+        "g_path_ms_per_apply": ms_g, "h_path_ms_per_apply": ms_h, "speedup_h_over_g": ms_g / ms_h,
+        "h_vs_g_rel_l2": diff, "g_bytes": info["g_bytes"], "h_bytes": info["h_bytes"],
+        "t_plan_s": t_plan, "t_h_build_s": t_build,
+        "stages_ms_g": st_g, "stages_ms_h": st_h, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "wideband":
         run_wideband(args)
+    elif args.config in ("holo", "holo-dense"):
+        run_holo(args)
     else:
         run_rimo(args)
 

@@ -214,10 +214,25 @@ rimo_status rimo_apply_phi_adj_phi(rimo_plan_t plan, const rimo_cfloat* x_dev,
 
 /*
  * Build the holographic matrices H_p = G_p^dagger G_p on the device (Section 3.3) and
- * switch rimo_apply_phi_adj_phi to them.  Needs a plan with stored G.
- * Synchronises `stream`.  Errors: UNSUPPORTED, OOM, BUDGET, CUDA.
+ * switch rimo_apply_phi_adj_phi (and rimo_psf) to them; Phi and Phi^dagger keep using G.
+ * H_p is Hermitian and stored once per cell pair: every grid cell that some visibility
+ * footprint covers gets a row of (H+1)^2 + H^2 complex entries, H = S_max - 1 (421 for
+ * S_max = 15), so it pays off where visibilities per covered cell are many.  Fails with
+ * BUDGET (before allocating the rows) when mem_budget_bytes is set and G plus H would
+ * exceed it.  A second call does nothing.  info.h_bytes reports the rows and patches.
+ * Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OOM, BUDGET, CUDA.
  */
 rimo_status rimo_build_holographic(rimo_plan_t plan, void* stream);
+
+/*
+ * Entries of the built holographic matrix of bin `bin`: out[q] = H_bin[c1][c2] for the
+ * cell pairs pairs[4q .. 4q+3] = (u1, v1, u2, v2) (grid cells, taken modulo the grid);
+ * zero where no footprint covers both cells.  pairs, out: host.  For tests and
+ * inspection (one small copy per entry).  Synchronises `stream`.
+ * Errors: INVALID_ARG, STATE (not built), CUDA.
+ */
+rimo_status rimo_plan_get_holographic(rimo_plan_t plan, int32_t bin, const int32_t* pairs, int64_t n,
+                                      rimo_cfloat* out, void* stream);
 
 /* PSF: out = Phi^dagger Phi delta, delta at pixel (ny/2, nx/2); unnormalised. */
 rimo_status rimo_psf(rimo_plan_t plan, rimo_cfloat* out_dev, void* stream);

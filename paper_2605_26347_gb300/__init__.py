@@ -169,6 +169,14 @@ class Plan:
     def build_holographic(self, stream=None):
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 
+    def holographic_entries(self, bin: int, pairs, stream=None) -> np.ndarray:
+        """H_bin[c1][c2] for rows (u1, v1, u2, v2) of `pairs` (rimo_plan_get_holographic)."""
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 4))
+        out = np.zeros(pr.shape[0], np.complex64)
+        _lib.check(self._lib.rimo_plan_get_holographic(self._h, int(bin), pr.ctypes.data, pr.shape[0],
+                                                        out.ctypes.data, _stream_ptr(stream)))
+        return out
+
 
 class Surrogate:
     """The kernel-surrogate MLP (rimo_surrogate_*): 3 -> 128 -> 128 -> 450, bf16 tensor cores."""

@@ -75,9 +75,9 @@ static void reset_schedulers(rimo_plan* p, cudaStream_t s) {
     RIMO_CUDA(cudaMemsetAsync(p->d_counter, 0, (size_t)p->P * sizeof(int32_t), s));
 }
 
-static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cudaStream_t s) {
+static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cudaStream_t s, bool holo = false) {
     prof_begin(p, ST_INV_COLS, s);
-    launch_inv_cols(p, b, p->d_AB, s);
+    launch_inv_cols_from(p, b, holo, p->d_AB, s);
     prof_end(p, p->bins[b].n1 > p->bins[b].n0 ? 2 : 1, s);
     prof_begin(p, ST_INV_ROWS, s);
     launch_inv_rows(p, b, p->d_AB, out, first ? 0 : 1, real_only, s);
@@ -124,8 +124,15 @@ void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
         fwd(p, b, x, s);
-        gtg(p, b, 2, nullptr, nullptr, s);
-        inv(p, b, out, first, real_only, s);
+        if (p->h_built) {
+            // H_p in place of G_p^dagger G_p (Section 3.3)
+            prof_begin(p, ST_HAPPLY, s);
+            launch_happly(p, b, s);
+            prof_end(p, p->bins[b].n1 > p->bins[b].n0 ? 1 : 0, s);
+        } else {
+            gtg(p, b, 2, nullptr, nullptr, s);
+        }
+        inv(p, b, out, first, real_only, s, p->h_built);
         first = false;
     }
     if (first) zero_image(p, (rimo_cfloat*)out, s);
@@ -217,12 +224,6 @@ rimo_status rimo_plan_status(rimo_plan_t p, void* stream) {
     RIMO_API_END
 }
 
-rimo_status rimo_build_holographic(rimo_plan_t p, void* stream) {
-    RIMO_API_BEGIN
-    check_plan(p);
-    (void)stream;
-    fail(RIMO_ERR_UNSUPPORTED, "holographic build not available in this build");
-    RIMO_API_END
-}
+
 
 }  // extern "C"

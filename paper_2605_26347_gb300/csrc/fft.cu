@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256) image_bound_kernel(const float2* __restri
         const float mt = 2.f * __uint_as_float(__ldcg(fx + FX_TMAX)) * __uint_as_float(__ldcg(fx + FX_T1)) * red[0];
         if (!(mt <= 3.4028234e38f)) atomicExch(status, 3);
         fx[FX_MAXTERM] = __float_as_uint(mt);
+        fx[FX_BX] = __float_as_uint(red[0]);
         fx[FX_COUNT] = 0u;
     }
 }
@@ -663,7 +664,7 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
 }
 
 template <int N>
-static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
+static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStream_t s) {
     constexpr int RB = inv_rows_per_block<N>();
     constexpr int C = cluster_of<RB>();
     const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 256;
@@ -672,8 +673,10 @@ static void inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
     const auto& br = p->bins[bin];
     if (br.n1 > br.n0) {
         FoldArgs F;
-        F.patch = p->d_patch;
-        F.slot = p->d_slot + (size_t)bin * ntile;
+        // grid-step patches (one per active tile, merged) or holographic-apply patches
+        // (one per needed tile): both cover [tile origin, + PW) on each axis
+        F.patch = holo ? p->d_hpatch : p->d_patch;
+        F.slot = (holo ? p->d_hslot : p->d_slot) + (size_t)bin * ntile;
         F.tiles = p->d_need_list + br.n0;
         F.Xh = p->d_X;
         F.ntu = ntu;
@@ -714,7 +717,10 @@ void launch_fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
     RIMO_DISPATCH_N(p->ny, fwd_cols<NN>(p, bin, At, X, s));
 }
 void launch_inv_cols(const rimo_plan* p, int bin, float2* B, cudaStream_t s) {
-    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, bin, B, s));
+    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, bin, false, B, s));
+}
+void launch_inv_cols_from(const rimo_plan* p, int bin, bool holographic, float2* B, cudaStream_t s) {
+    RIMO_DISPATCH_N(p->ny, inv_cols<NN>(p, bin, holographic, B, s));
 }
 void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int accumulate,
                      int real_only, cudaStream_t s) {

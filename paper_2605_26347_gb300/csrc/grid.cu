@@ -90,7 +90,9 @@ struct GtgArgs {
     int chunk_bytes;
     int nbuf;               // ring depth in use, 2..GTG_NBUF
     int* status;
-    const uint32_t* fx;     // fixed-point bounds (maxterm of this apply)
+    const uint32_t* fx;     // fixed-point bounds (tap bounds; maxterm of a Phi^dagger apply)
+    const uint8_t* need;    // [tile] of this bin: some footprint reaches the tile
+    int ntv, shift;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     int* Ahi = reinterpret_cast<int*>(Xs + (GATHER ? npatch : 0));  // [cell][re, im] words
     int* Alo = Ahi + (SCATTER ? 2 * npatch : 0);
     __shared__ volatile int s_abort;
+    __shared__ float s_xmax[GTG_CONSUMERS];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, cb = blockIdx.x;
@@ -303,8 +306,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         const TileDesc td = A.units[slot];
         const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
-        float s1 = 1.f, inv_s1 = 1.f;
-        if (SCATTER) fx_scale(__uint_as_float(__ldg(A.fx + FX_MAXTERM)), td.ve - td.vb, s1, inv_s1);
+        float xm = 0.f;
         for (int a = warp; a < PW; a += GTG_CONSUMERS) {
             int gu = u0 + a;
             if (gu >= A.gx) gu -= A.gx;
@@ -312,7 +314,11 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 if (GATHER) {
                     int gv = v0 + b;
                     if (gv >= A.gy) gv -= A.gy;
-                    Xs[a * PW + b] = A.X[(size_t)gu * A.gy + gv];
+                    // cells of tiles no footprint reaches hold no grid values of this bin
+                    const float2 x = A.need[(gu >> A.shift) * A.ntv + (gv >> A.shift)]
+                                         ? A.X[(size_t)gu * A.gy + gv] : make_float2(0.f, 0.f);
+                    Xs[a * PW + b] = x;
+                    xm = fmaxf(xm, fabsf(x.x) + fabsf(x.y));
                 }
                 if (SCATTER) {
                     reinterpret_cast<int2*>(Ahi)[a * PW + b] = make_int2(0, 0);
@@ -320,7 +326,24 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 }
             }
         }
+        if (MODE == 2) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+            if (lane == 0) s_xmax[warp] = xm;
+        }
         consumers_sync();
+        float s1 = 1.f, inv_s1 = 1.f;
+        if (MODE == 2) {
+            // per-unit bound: a de-gridded y of this unit has |y.x| + |y.y| <= 2 T1 max|X|_1
+            // over the patch, a contribution component at most tmax times that (margin 2)
+            float xmax = 0.f;
+#pragma unroll
+            for (int w = 0; w < GTG_CONSUMERS; ++w) xmax = fmaxf(xmax, s_xmax[w]);
+            const float mt = 4.f * __uint_as_float(__ldg(A.fx + FX_TMAX)) * __uint_as_float(__ldg(A.fx + FX_T1)) * xmax;
+            fx_scale(mt, td.ve - td.vb, s1, inv_s1);
+        } else if (SCATTER) {
+            fx_scale(__uint_as_float(__ldg(A.fx + FX_MAXTERM)), td.ve - td.vb, s1, inv_s1);
+        }
         for (int c = 0; c < nchunks; ++c, ++g) {
             const uint32_t b = g % NB, par = (g / NB) & 1;
             if (!s_abort && !mbar_wait_bounded(&full[b], par)) {
@@ -399,6 +422,9 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.chunk_bytes = p->chunk_bytes;
     A.status = p->d_status;
     A.fx = p->d_fx;
+    A.ntv = p->gy / p->TS;
+    A.shift = p->TS == 64 ? 6 : 5;
+    A.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * A.ntv;
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
     A.nbuf = GTG_NBUF;
     while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf) > limit) --A.nbuf;

@@ -134,6 +134,21 @@ struct rimo_plan {
     uint32_t* d_fx = nullptr;      // fixed-point grid-step bounds (layout: rimo::FX_*)
     int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     int device = 0;                // CUDA device the plan lives on
+    std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
+
+    // holographic matrices (Section 3.3), once rimo_build_holographic has run.  Each pair of
+    // cells (c1, c2) of H_p = G_p^dagger G_p with |c2 - c1| <= H per axis is stored once, at
+    // its owner: the cell at the top-left corner of the pair's bounding box (see hmat.cu).
+    bool h_built = false;
+    int h_ne = 0;                         // entries per owner cell: (H+1)^2 + H^2
+    std::vector<float2*> d_hrows;         // per bin: [owner][h_ne]
+    std::vector<uint32_t*> d_htmax;       // per bin: [needed tile] max |h.x| + |h.y| (float bits)
+    std::vector<uint32_t*> d_hbits;       // per bin: [needed tile][TS*TS/32] covered cells
+    std::vector<int64_t*> d_hoff;         // per bin: [needed tile + 1] first owner of the tile
+    std::vector<std::vector<int64_t>> hoff_host;
+    int32_t* d_hslot = nullptr;           // [bin][tile] -> needed-tile index in the bin, or -1
+    float2* d_hpatch = nullptr;           // H-apply output patches of one bin [needed tile][PW*PW]
+    int32_t* d_hent = nullptr;            // entry table (type << 16 | a << 8 | |b|)
     float2* d_AB = nullptr;    // half-transformed intermediates (2 nx ny)
     float2* d_delta = nullptr; // delta image for the PSF
     rimo::DevTables tab;
@@ -154,8 +169,22 @@ namespace rimo {
 
 void* dev_alloc(rimo_plan* p, size_t bytes);
 
+// Device copy of a host vector, owned by the plan (freed in rimo_plan_destroy).
+template <class T>
+T* upload_vec(rimo_plan* p, const std::vector<T>& v, cudaStream_t s) {
+    T* d = (T*)dev_alloc(p, v.size() * sizeof(T));
+    if (!v.empty()) {
+        const cudaError_t e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) fail(RIMO_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    return d;
+}
+
 enum Stage { ST_FWD_ROWS = 0, ST_FWD_COLS = 1, ST_CLEAR = 2, ST_GTG = 3, ST_INV_COLS = 4,
              ST_INV_ROWS = 5, ST_GBUILD = 6, ST_HBUILD = 7, ST_HAPPLY = 8, ST_MLP = 9, ST_BOUND = 10 };
+
+constexpr int FX_HMAX = 5;      // max over entries of H of |h.x| + |h.y| (float bits)
+constexpr int FX_BX = 6;        // image bound B_x of the current Phi^dagger Phi apply (float)
 
 // Fixed-point grid step.  The grid step accumulates each tile patch in two 32-bit integer
 // words per real number (hi: the contribution scaled by a power of two s and rounded;
@@ -200,5 +229,10 @@ void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only
 // Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);
 void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s);
+// Holographic apply of bin `bin` (forward grid in d_X -> output patches in d_hpatch).
+void launch_happly(const rimo_plan* p, int bin, cudaStream_t s);
+// Fold of the patches of bin `bin` (GTG's or the holographic ones) into d_X and the
+// inverse cols pass.
+void launch_inv_cols_from(const rimo_plan* p, int bin, bool holographic, float2* B, cudaStream_t s);
 
 }  // namespace rimo

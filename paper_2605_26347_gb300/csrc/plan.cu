@@ -527,6 +527,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
             p->bins[b].n1 = (int32_t)nl.size();
         }
         p->d_need_list = upload(p, nl, s);
+        p->need_host = nl;
     }
     p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
