@@ -77,3 +77,18 @@ def test_budget_refuses_the_build():
     with pytest.raises(pkg.RimoError) as e:
         plan2.build_holographic()
     assert e.value.status == 3
+
+
+def test_dense_coverage_parity():
+    # many visibilities per grid cell (the regime H is for): 64^2 image, 128^2 grid,
+    # 150k visibilities over 2 bins, about 9 per covered cell
+    uvw = synth.make_uvw(150_000, 28_800, 1.28e9, 93) * np.array([0.25, 0.25, 1.0])
+    fov = math.radians(1.0)
+    plan, op = both(uvw, 64, 64, fov, fov, n_wbins=2)
+    x = synth.make_sky(64, 94)
+    g_path = to_host(plan.phi_adj_phi(to_dev(x)))
+    plan.build_holographic()
+    h_path = to_host(plan.phi_adj_phi(to_dev(x)))
+    ref = op.phi_adj_phi(x.astype(np.complex128))
+    assert rel(g_path, ref) < TOL
+    assert rel(h_path, ref) < TOL
