@@ -377,6 +377,37 @@ rimo_status rimo_batch_info(rimo_batch_t batch, int32_t* n_plans, int64_t* captu
 rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
                                void* stream, int32_t* tile_out, double* ms_out);
 
+/*
+ * Kernel surrogate as the plan's tile generator.  A plan created with mode
+ * RIMO_MODE_SURROGATE (kb_support + max_wsupport - 1 must be 15) places every visibility
+ * with the largest support (15 x 15 tiles), keeps one Fourier block per w-bin and stores
+ * no G: each apply generates one bin's tiles at a time with the attached network into a
+ * scratch the size of the largest bin, then grids them as the stored-G path does.
+ * rimo_plan_set_surrogate attaches s (not owned; it must outlive its use, and one
+ * surrogate must not serve two applies at once) and allocates the generation buffers.
+ * Applies of a surrogate plan without a surrogate fail with STATE; rimo_plan_get_tiles,
+ * rimo_build_holographic and the allocation-free apply return UNSUPPORTED.
+ * Errors: INVALID_ARG (plan not in surrogate mode, other device), OOM, CUDA.
+ */
+rimo_status rimo_plan_set_surrogate(rimo_plan_t plan, rimo_surrogate_t s);
+
+/*
+ * Train s on exact tiles: n_samples visibilities of `exact` (a stored-G plan with 15 x 15
+ * tiles; smaller supports are embedded at the centre) drawn uniformly by a counter-based
+ * SplitMix64 from `seed`, inputs (2 phi_u - 1, 2 phi_v - 1, w_r / w_scale) with w_scale =
+ * the plan's largest |w_r|; `steps` Adam steps on batches of `batch` (a multiple of 128)
+ * drawn from the samples, learning rate decaying from lr to lr / 100 (cosine).  losses
+ * (host, `steps` values, may be NULL): each step's mean squared error before the update.
+ * Sets the surrogate's w_scale.  Synchronises `stream`.  Errors: INVALID_ARG, OOM,
+ * TIMEOUT, CUDA.
+ */
+rimo_status rimo_surrogate_fit(rimo_surrogate_t s, rimo_plan_t exact, int64_t n_samples, int32_t steps,
+                               int32_t batch, float lr, uint64_t seed, float* losses, void* stream);
+/* The w_r normalisation of the inputs (0 until fitted or set; then the plan's largest
+ * |w_r| is used). */
+rimo_status rimo_surrogate_get_w_scale(rimo_surrogate_t s, float* w_scale);
+rimo_status rimo_surrogate_set_w_scale(rimo_surrogate_t s, float w_scale);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rimo_last_error(void);
 

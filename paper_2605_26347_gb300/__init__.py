@@ -169,6 +169,11 @@ class Plan:
     def build_holographic(self, stream=None):
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 
+    def set_surrogate(self, sur: "Surrogate") -> None:
+        """rimo_plan_set_surrogate: generate this (surrogate-mode) plan's tiles with `sur`."""
+        _lib.check(self._lib.rimo_plan_set_surrogate(self._h, sur._h))
+        self._sur = sur  # keep it alive as long as the plan uses it
+
     def holographic_entries(self, bin: int, pairs, stream=None) -> np.ndarray:
         """H_bin[c1][c2] for rows (u1, v1, u2, v2) of `pairs` (rimo_plan_get_holographic)."""
         pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 4))
@@ -242,6 +247,24 @@ class Surrogate:
                                                        float(lr), C.byref(loss) if want_loss else None,
                                                        _stream_ptr(stream)))
         return float(loss.value) if want_loss else None
+
+    def fit(self, exact_plan, n_samples: int, steps: int, batch: int = 1024, lr: float = 1e-3,
+            seed: int = 0, stream=None) -> np.ndarray:
+        """rimo_surrogate_fit on the exact tiles of `exact_plan`; returns the per-step losses."""
+        losses = np.zeros(int(steps), np.float32)
+        _lib.check(self._lib.rimo_surrogate_fit(self._h, exact_plan._h, int(n_samples), int(steps), int(batch),
+                                                float(lr), int(seed), losses.ctypes.data, _stream_ptr(stream)))
+        return losses
+
+    @property
+    def w_scale(self) -> float:
+        v = C.c_float()
+        _lib.check(self._lib.rimo_surrogate_get_w_scale(self._h, C.byref(v)))
+        return float(v.value)
+
+    @w_scale.setter
+    def w_scale(self, value: float) -> None:
+        _lib.check(self._lib.rimo_surrogate_set_w_scale(self._h, float(value)))
 
 
 class Batch:

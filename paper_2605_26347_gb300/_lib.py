@@ -105,6 +105,10 @@ _PROTOS = {
     "rimo_batch_apply_phi_adj_phi": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "rimo_batch_info": (C.c_int, [_P, _P, _P]),
     "rimo_autotune_tile": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P]),
+    "rimo_plan_set_surrogate": (C.c_int, [_P, _P]),
+    "rimo_surrogate_fit": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P, _P]),
+    "rimo_surrogate_get_w_scale": (C.c_int, [_P, C.POINTER(C.c_float)]),
+    "rimo_surrogate_set_w_scale": (C.c_int, [_P, C.c_float]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

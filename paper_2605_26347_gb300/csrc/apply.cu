@@ -85,14 +85,27 @@ static void inv(rimo_plan* p, int b, float2* out, bool first, int real_only, cud
 }
 
 static void gtg(rimo_plan* p, int b, int mode, const float2* y_in, float2* y_out, cudaStream_t s) {
+    if (p->mode == RIMO_MODE_SURROGATE) {
+        prof_begin(p, ST_MLP, s);
+        const int nl = surrogate_generate(p, b, s);  // this bin's tiles into the tap scratch
+        prof_end(p, nl, s);
+    }
     prof_begin(p, ST_GTG, s);
     launch_gtg(p, b, mode, y_in, y_out, s);
     const bool merge = mode != 0 && p->bins[b].m1 > p->bins[b].m0;
     prof_end(p, gtg_launches(p, b, mode) + (merge ? 1 : 0), s);
 }
 
-void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {
+static void begin_apply(rimo_plan* p, cudaStream_t s) {
     reset_schedulers(p, s);
+    if (p->mode == RIMO_MODE_SURROGATE) {
+        if (!p->sur) fail(RIMO_ERR_STATE, "surrogate plan without a surrogate (rimo_plan_set_surrogate)");
+        reset_surrogate_bounds(p, s);
+    }
+}
+
+void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {
+    begin_apply(p, s);
     for (int b = 0; b < p->P; ++b) {
         if (bin_empty(p, b)) continue;
         fwd(p, b, x, s);
@@ -102,7 +115,7 @@ void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {
 
 void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
     bool first = true;
-    reset_schedulers(p, s);
+    begin_apply(p, s);
     prof_begin(p, ST_BOUND, s);
     launch_y_bound(p, y, s);
     prof_end(p, p->M > 0 ? 1 : 0, s);
@@ -117,7 +130,7 @@ void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
 
 void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s) {
     bool first = true;
-    reset_schedulers(p, s);
+    begin_apply(p, s);
     prof_begin(p, ST_BOUND, s);
     launch_image_bound(p, x, s);
     prof_end(p, 1, s);

@@ -613,6 +613,7 @@ extern "C" {
 rimo_status rimo_build_holographic(rimo_plan_t p, void* stream) {
     RIMO_API_BEGIN
     if (!p) fail(RIMO_ERR_INVALID_ARG, "null plan");
+    if (p->mode == RIMO_MODE_SURROGATE) fail(RIMO_ERR_UNSUPPORTED, "a surrogate plan stores no G to build H from");
     if (!p->h_built) build_holographic(p, (cudaStream_t)stream);
     RIMO_API_END
 }

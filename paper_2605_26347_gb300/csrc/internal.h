@@ -136,6 +136,11 @@ struct rimo_plan {
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
 
+    // kernel surrogate (mode RIMO_MODE_SURROGATE): tiles generated per bin at apply time
+    struct rimo_surrogate* sur = nullptr;  // attached by rimo_plan_set_surrogate (not owned)
+    float2* d_sur_taps = nullptr;          // one bin's taps, laid out like its G block
+    int64_t sur_taps_bytes = 0;
+
     // holographic matrices (Section 3.3), once rimo_build_holographic has run.  Each pair of
     // cells (c1, c2) of H_p = G_p^dagger G_p with |c2 - c1| <= H per axis is stored once, at
     // its owner: the cell at the top-left corner of the pair's bounding box (see hmat.cu).
@@ -229,6 +234,10 @@ void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only
 // Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);
 void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s);
+// Kernel surrogate: fill d_sur_taps with the MLP's tiles of bin `bin` (and the tap bounds
+// of the fixed-point grid step); reset_surrogate_bounds clears those bounds for an apply.
+int surrogate_generate(rimo_plan* p, int bin, cudaStream_t s);  // returns kernel launches
+void reset_surrogate_bounds(rimo_plan* p, cudaStream_t s);
 // Holographic apply of bin `bin` (forward grid in d_X -> output patches in d_hpatch).
 void launch_happly(const rimo_plan* p, int bin, cudaStream_t s);
 // Fold of the patches of bin `bin` (GTG's or the holographic ones) into d_X and the

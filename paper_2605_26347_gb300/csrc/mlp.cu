@@ -471,6 +471,8 @@ void Mlp::step(const float* X, const float* T, int B, float lr, cudaStream_t s) 
 // C ABI
 struct rimo_surrogate {
     rimo::Mlp mlp;
+    float w_scale = 0.f;        // input normalisation of w_r (set by rimo_surrogate_fit)
+    float* Xin = nullptr;       // generation inputs [SUR_SUB][3]
 };
 
 namespace rimo {
@@ -513,6 +515,135 @@ using namespace rimo;
         set_last_error(e.what());     \
         return RIMO_ERR_OOM;          \
     }
+
+namespace rimo {
+
+constexpr int SUR_SUB = 1 << 16;  // visibilities per generation sub-batch (a multiple of 128)
+constexpr int SUR_S = 15;         // tile side the network outputs
+constexpr int SUR_TAPS = SUR_S * SUR_S;
+
+// SplitMix64 (Steele, Lea, Flood 2014): counter-based draws for the training samples.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// network inputs (2 phi_u - 1, 2 phi_v - 1, w_r / w_scale) of sorted visibilities
+// [v0, v0 + n); rows n .. B-1 repeat the last visibility (their outputs are not used)
+__global__ void sur_inputs_kernel(const float* __restrict__ phiu, const float* __restrict__ phiv,
+                                  const float* __restrict__ wr, int64_t v0, int n, int B, float inv_w, float* X) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    const int64_t k = v0 + (j < n ? j : n - 1);
+    X[3 * j + 0] = 2.f * phiu[k] - 1.f;
+    X[3 * j + 1] = 2.f * phiv[k] - 1.f;
+    X[3 * j + 2] = wr[k] * inv_w;
+}
+
+// one warp per visibility: tile q = (Y[q] + b3[q], Y[225 + q] + b3[225 + q]) into the tap
+// scratch at the visibility's offset, plus the tap bounds of the fixed-point grid step
+__global__ void sur_outputs_kernel(const float* __restrict__ Y, const float* __restrict__ b3,
+                                   const VisMeta* __restrict__ meta, int64_t v0, int n, float2* __restrict__ taps,
+                                   uint32_t* fx) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const float* y = Y + (size_t)warp * MLP_OUT_PAD;
+    float2* t = taps + meta[v0 + warp].off;
+    float tmax = 0.f, tsum = 0.f;
+    for (int q = lane; q < SUR_TAPS + 1; q += 32) {  // 225 taps and the even-count pad
+        float2 v = make_float2(0.f, 0.f);
+        if (q < SUR_TAPS) v = make_float2(y[q] + b3[q], y[SUR_TAPS + q] + b3[SUR_TAPS + q]);
+        t[q] = v;
+        const float m = fabsf(v.x) + fabsf(v.y);
+        tmax = fmaxf(tmax, m);
+        tsum += m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    }
+    if (lane == 0) {
+        atomicMax(fx + FX_TMAX, __float_as_uint(tmax));
+        atomicMax(fx + FX_T1, __float_as_uint(tsum));
+    }
+}
+
+void reset_surrogate_bounds(rimo_plan* p, cudaStream_t s) {
+    RIMO_CUDA(cudaMemsetAsync(p->d_fx + FX_TMAX, 0, 2 * sizeof(uint32_t), s));  // FX_TMAX, FX_T1
+}
+
+int surrogate_generate(rimo_plan* p, int bin, cudaStream_t s) {
+    rimo_surrogate* sur = p->sur;
+    Mlp& m = sur->mlp;
+    const float ws = sur->w_scale > 0.f ? sur->w_scale : (p->info.wr_max > 0 ? (float)p->info.wr_max : 1.f);
+    const int64_t vb = p->bins[bin].vb, ve = p->bins[bin].ve;
+    int launches = 0;
+    for (int64_t v0 = vb; v0 < ve; v0 += SUR_SUB) {
+        const int n = (int)std::min<int64_t>(SUR_SUB, ve - v0);
+        const int B = (n + 127) / 128 * 128;
+        sur_inputs_kernel<<<(B + 255) / 256, 256, 0, s>>>(p->d_phiu, p->d_phiv, p->d_wr, v0, n, B, 1.f / ws, sur->Xin);
+        m.forward(sur->Xin, B, s);
+        sur_outputs_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(m.Y, m.P + MLP_OFF_B3, p->d_meta, v0, n,
+                                                                 p->d_sur_taps, p->d_fx);
+        launches += 6;
+    }
+    return launches;
+}
+
+// training sample i: a visibility k drawn uniformly, its inputs, and its exact tile embedded
+// at the centre of 15 x 15 (a smaller support S sits at offset (15 - S) / 2)
+__global__ void sur_dataset_kernel(const VisMeta* __restrict__ meta, float2* const* __restrict__ gblk,
+                                   const float* __restrict__ phiu, const float* __restrict__ phiv,
+                                   const float* __restrict__ wr, int64_t M, uint64_t seed, int64_t n, float inv_w,
+                                   float* X, float* T) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t k = (int64_t)(splitmix64(seed + (uint64_t)i) % (uint64_t)M);
+    const VisMeta mt = meta[k];
+    const int S = (mt.pos >> 16) & 255, off = (SUR_S - S) / 2;
+    const float2* G = gblk[mt.pos >> 24] + mt.off;
+    if (lane == 0) {
+        X[3 * i + 0] = 2.f * phiu[k] - 1.f;
+        X[3 * i + 1] = 2.f * phiv[k] - 1.f;
+        X[3 * i + 2] = wr[k] * inv_w;
+    }
+    float* t = T + (size_t)i * MLP_OUT;
+    for (int q = lane; q < SUR_TAPS; q += 32) {
+        const int a = q / SUR_S - off, b = q % SUR_S - off;
+        const float2 v = (a >= 0 && a < S && b >= 0 && b < S) ? G[a * S + b] : make_float2(0.f, 0.f);
+        t[q] = v.x;
+        t[SUR_TAPS + q] = v.y;
+    }
+}
+
+__global__ void sur_batch_kernel(const float* __restrict__ X, const float* __restrict__ T, int64_t n, uint64_t seed,
+                                 int B, float* Xb, float* Tb) {
+    const int j = blockIdx.x;
+    const int64_t i = (int64_t)(splitmix64(seed + (uint64_t)j) % (uint64_t)n);
+    for (int e = threadIdx.x; e < MLP_OUT; e += blockDim.x) Tb[(size_t)j * MLP_OUT + e] = T[(size_t)i * MLP_OUT + e];
+    if (threadIdx.x < 3) Xb[3 * j + threadIdx.x] = X[3 * i + threadIdx.x];
+}
+
+struct DevScratch {
+    std::vector<void*> v;
+    void* get(size_t bytes) {
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            fail(RIMO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes for the training set failed");
+        }
+        v.push_back(ptr);
+        return ptr;
+    }
+    ~DevScratch() {
+        for (void* ptr : v) cudaFree(ptr);
+    }
+};
+
+}  // namespace rimo
 
 extern "C" {
 
@@ -597,6 +728,79 @@ rimo_status rimo_surrogate_train_step(rimo_surrogate_t s, const float* x, const 
         RIMO_CUDA(cudaStreamSynchronize(st));
         *loss = l / ((float)B * MLP_OUT);
     }
+    SUR_END
+}
+
+
+rimo_status rimo_plan_set_surrogate(rimo_plan_t p, rimo_surrogate_t s) {
+    SUR_BEGIN
+    if (!p || !s) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    if (p->mode != RIMO_MODE_SURROGATE) fail(RIMO_ERR_INVALID_ARG, "the plan was not created in surrogate mode");
+    int dev = 0;
+    RIMO_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) fail(RIMO_ERR_INVALID_ARG, "plan and surrogate on different devices");
+    // everything the generation needs is allocated here, not during an apply
+    s->mlp.reserve(SUR_SUB);
+    if (!s->Xin) s->Xin = (float*)s->mlp.alloc((size_t)SUR_SUB * 3 * sizeof(float));
+    p->sur = s;
+    SUR_END
+}
+
+rimo_status rimo_surrogate_fit(rimo_surrogate_t s, rimo_plan_t exact, int64_t n_samples, int32_t steps,
+                               int32_t batch, float lr, uint64_t seed, float* losses, void* stream) {
+    SUR_BEGIN
+    if (!s || !exact) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    if (exact->mode == RIMO_MODE_SURROGATE || exact->d_gblocks.empty())
+        fail(RIMO_ERR_INVALID_ARG, "training needs a plan with stored exact tiles");
+    if (exact->J + exact->prm.max_wsupport - 1 != SUR_S)
+        fail(RIMO_ERR_INVALID_ARG, "training tiles must be 15 x 15 (kb_support + max_wsupport - 1 = 15)");
+    if (n_samples <= 0 || steps <= 0 || !(lr > 0.f)) fail(RIMO_ERR_INVALID_ARG, "n_samples, steps, lr must be > 0");
+    check_batch(batch);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float ws = exact->info.wr_max > 0 ? (float)exact->info.wr_max : 1.f;
+    DevScratch tmp;
+    float* X = (float*)tmp.get((size_t)n_samples * 3 * sizeof(float));
+    float* T = (float*)tmp.get((size_t)n_samples * MLP_OUT * sizeof(float));
+    float* Xb = (float*)tmp.get((size_t)batch * 3 * sizeof(float));
+    float* Tb = (float*)tmp.get((size_t)batch * MLP_OUT * sizeof(float));
+    float* L = (float*)tmp.get((size_t)steps * sizeof(float));
+    const uint64_t sample_seed = splitmix64(seed ^ 0x5EEDull);
+    sur_dataset_kernel<<<(unsigned)((n_samples * 32 + 255) / 256), 256, 0, st>>>(
+        exact->d_meta, exact->d_gblock_ptrs, exact->d_phiu, exact->d_phiv, exact->d_wr, exact->M, sample_seed,
+        n_samples, 1.f / ws, X, T);
+    RIMO_CUDA(cudaGetLastError());
+    s->mlp.reserve(batch);
+    for (int k = 0; k < steps; ++k) {
+        // cosine decay from lr to lr / 100
+        const float lr_k = lr * (0.01f + 0.99f * 0.5f * (1.f + std::cos(3.14159265358979f * (float)k / (float)steps)));
+        sur_batch_kernel<<<batch, 128, 0, st>>>(X, T, n_samples, splitmix64(seed + 0x9E37ull * (uint64_t)(k + 1)),
+                                                 batch, Xb, Tb);
+        s->mlp.step(Xb, Tb, batch, lr_k, st);
+        RIMO_CUDA(cudaMemcpyAsync(L + k, s->mlp.loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    RIMO_CUDA(cudaGetLastError());
+    check_status(s->mlp, st);
+    if (losses) {
+        RIMO_CUDA(cudaMemcpyAsync(losses, L, (size_t)steps * sizeof(float), cudaMemcpyDeviceToHost, st));
+        RIMO_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < steps; ++k) losses[k] /= (float)batch * MLP_OUT;
+    }
+    RIMO_CUDA(cudaStreamSynchronize(st));
+    s->w_scale = ws;
+    SUR_END
+}
+
+rimo_status rimo_surrogate_get_w_scale(rimo_surrogate_t s, float* w_scale) {
+    SUR_BEGIN
+    if (!s || !w_scale) fail(RIMO_ERR_INVALID_ARG, "null argument");
+    *w_scale = s->w_scale;
+    SUR_END
+}
+
+rimo_status rimo_surrogate_set_w_scale(rimo_surrogate_t s, float w_scale) {
+    SUR_BEGIN
+    if (!s || !(w_scale > 0.f)) fail(RIMO_ERR_INVALID_ARG, "null surrogate or w_scale <= 0");
+    s->w_scale = w_scale;
     SUR_END
 }
 

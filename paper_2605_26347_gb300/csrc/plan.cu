@@ -243,8 +243,10 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     fill_estimate(&p->info, ch, M, p->L);
     p->P = ch.P;
     p->mode = ch.mode;
-    if (p->mode == RIMO_MODE_SURROGATE || p->mode == RIMO_MODE_ONTHEFLY)
-        fail(RIMO_ERR_UNSUPPORTED, "on-the-fly kernel modes are created with their own entry point");
+    if (p->mode == RIMO_MODE_ONTHEFLY) fail(RIMO_ERR_UNSUPPORTED, "exact on-the-fly kernels are not built");
+    const bool surrogate = p->mode == RIMO_MODE_SURROGATE;
+    if (surrogate && (q.kb_support + q.max_wsupport - 1 != 15))
+        fail(RIMO_ERR_UNSUPPORTED, "the kernel surrogate generates 15 x 15 tiles: kb_support + max_wsupport - 1 must be 15");
     if (p->mode == RIMO_MODE_HOLOGRAPHIC) p->holographic = false;  // G first, H on request
 
     // ---- w-bins on the subset, every visibility to its nearest bin (Section 3.1)
@@ -271,7 +273,8 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     int max_sw = 1;
     planner::parallel_for(M, [&](int64_t b, int64_t e) {
         for (int64_t k = b; k < e; ++k) {
-            int Sw = tab[planner::support_bin(std::fabs(wr[k]), wr_max)];
+            // the surrogate generates every tile at the largest support
+            int Sw = surrogate ? q.max_wsupport : tab[planner::support_bin(std::fabs(wr[k]), wr_max)];
             sw[k] = Sw;
             int h = (Sw - 1) / 2;
             double tu = uvw[3 * k + 0] * (2.0 * q.fov_x) - J / 2.0;
@@ -373,6 +376,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     double limit = q.block_bytes_max > 0 ? (double)q.block_bytes_max : 8.0 * 1073741824.0;
     if (q.n_blocks > 0) limit = std::ceil(total_bytes / q.n_blocks);
     limit = std::max(limit, std::ceil(total_bytes / 200.0));
+    if (surrogate) limit = 1e300;  // one block per bin: its taps are generated into one scratch
     std::vector<VisMeta> meta(M);
     std::vector<float> wr_s(M), pu_s(M), pv_s(M);
     p->bins.assign(P, BinRange());
@@ -497,11 +501,22 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->d_phiu = upload(p, pu_s, s);
     p->d_phiv = upload(p, pv_s, s);
     int64_t gbytes = 0;
-    for (int64_t bb : p->block_bytes) {
-        p->d_gblocks.push_back((float2*)dev_alloc(p, (size_t)std::max<int64_t>(bb, 16)));
-        gbytes += bb;
+    std::vector<float2*> ptrs;
+    if (surrogate) {
+        // no stored G: every bin's (single) block points at one scratch that the surrogate
+        // refills for each bin of each apply
+        int64_t mx = 16;
+        for (int64_t bb : p->block_bytes) mx = std::max(mx, bb);
+        p->d_sur_taps = (float2*)dev_alloc(p, (size_t)mx);
+        p->sur_taps_bytes = mx;
+        for (size_t i = 0; i < p->block_bytes.size(); ++i) ptrs.push_back(p->d_sur_taps);
+    } else {
+        for (int64_t bb : p->block_bytes) {
+            p->d_gblocks.push_back((float2*)dev_alloc(p, (size_t)std::max<int64_t>(bb, 16)));
+            gbytes += bb;
+        }
+        ptrs = p->d_gblocks;
     }
-    std::vector<float2*> ptrs(p->d_gblocks);
     p->d_gblock_ptrs = upload(p, ptrs, s);
     const size_t grid_elems = (size_t)gx * gy;
     p->d_X = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
@@ -553,14 +568,16 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->info.K = K;
     p->info.g_bytes = gbytes + (int64_t)M * (int64_t)sizeof(VisMeta);
     p->info.scratch_bytes = (int64_t)(grid_elems + 3 * (size_t)p->nx * p->ny +
-                                      (size_t)p->max_tiles_bin * p->PW * p->PW) * 8;
+                                      (size_t)p->max_tiles_bin * p->PW * p->PW) * 8 + p->sur_taps_bytes;
     p->info.n_blocks = (int32_t)p->block_bytes.size();
     p->info.n_tiles = n_active;
 
-    // ---- stage 3: precompute G on the device
-    prof_begin(p, ST_GBUILD, s);
-    launch_gbuild(p, s);
-    prof_end(p, 1, s);
+    // ---- stage 3: precompute G on the device (the surrogate generates it at apply time)
+    if (!surrogate) {
+        prof_begin(p, ST_GBUILD, s);
+        launch_gbuild(p, s);
+        prof_end(p, 1, s);
+    }
     RIMO_CUDA(cudaGetLastError());
     RIMO_CUDA(cudaStreamSynchronize(s));
 }
@@ -667,6 +684,8 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
     try {
         if (!p || (n > 0 && (!idx || !g0 || !h0 || !S || !taps)) || n < 0)
             fail(RIMO_ERR_INVALID_ARG, "null pointer or n < 0");
+        if (p->mode == RIMO_MODE_SURROGATE)
+            fail(RIMO_ERR_UNSUPPORTED, "a surrogate plan stores no tiles (they are generated per bin at apply time)");
         cudaStream_t s = (cudaStream_t)stream;
         for (int64_t q = 0; q < n; ++q) {
             if (idx[q] < 0 || idx[q] >= p->M) fail(RIMO_ERR_INVALID_ARG, "visibility index out of range");

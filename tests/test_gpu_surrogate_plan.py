@@ -1,0 +1,82 @@
+"""The kernel surrogate as a plan's tile generator, trained on the exact tiles.
+
+The network replaces stored G: tiles are generated per w-bin at apply time.  The exact
+stored-G plan judges its error; the gain of the trained network is measured against the
+method without it, i.e. the same gridding without the residual w-kernels (KB
+interpolation only, max_wsupport = 1), and against the untrained network.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from parity_util import rel, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import paper_2605_26347_gb300 as pkg
+    w = synth.make_config(1)
+    fov = w.fov_rad
+    kw = dict(n_wbins=4, w_norm_frac=1.0)               # every tile 15 x 15 (S_w = 9)
+    exact = pkg.Plan(w.uvw, pkg.default_params(256, 256, fov, fov, **kw))
+    sur = pkg.Surrogate(seed=1)
+    losses = sur.fit(exact, n_samples=w.uvw.shape[0], steps=3000, batch=1024, lr=2e-3, seed=7)
+    splan = pkg.Plan(w.uvw, pkg.default_params(256, 256, fov, fov, mode=pkg.MODE_SURROGATE, **kw))
+    splan.set_surrogate(sur)
+    return w, exact, sur, splan, losses
+
+
+def test_training_reduces_the_loss(trained):
+    _, _, sur, _, losses = trained
+    assert np.all(np.isfinite(losses))
+    assert losses[-100:].mean() < 0.05 * losses[:10].mean()
+    assert sur.w_scale > 0
+
+
+def test_surrogate_path_beats_the_method_without_w_kernels(trained):
+    import paper_2605_26347_gb300 as pkg
+    w, exact, _, splan, _ = trained
+    fov = w.fov_rad
+    x = to_dev(w.sky)
+    ref = to_host(exact.phi_adj_phi(x))
+    got = to_host(splan.phi_adj_phi(x))
+    kb_only = pkg.Plan(w.uvw, pkg.default_params(256, 256, fov, fov, n_wbins=4, max_wsupport=1))
+    none = to_host(kb_only.phi_adj_phi(x))
+    e_sur, e_none = rel(got, ref), rel(none, ref)
+    print(f"surrogate vs exact {e_sur:.3e}, without w-kernels {e_none:.3e}")
+    assert e_sur < 0.5 * e_none
+    y_ref = to_host(exact.phi(x))
+    assert rel(to_host(splan.phi(x)), y_ref) < rel(to_host(kb_only.phi(x)), y_ref)
+    # the untrained network is no substitute
+    raw = pkg.Surrogate(seed=1)
+    splan2 = pkg.Plan(w.uvw, pkg.default_params(256, 256, fov, fov, mode=pkg.MODE_SURROGATE, n_wbins=4,
+                                                w_norm_frac=1.0))
+    splan2.set_surrogate(raw)
+    assert rel(to_host(splan2.phi_adj_phi(x)), ref) > 10 * e_sur
+
+
+def test_surrogate_plan_stores_no_g(trained):
+    import paper_2605_26347_gb300 as pkg
+    w, exact, _, splan, _ = trained
+    gi, si = exact.info(), splan.info()
+    assert si["g_bytes"] < 0.01 * gi["g_bytes"]
+    with pytest.raises(pkg.RimoError) as e:
+        splan.tiles([0])
+    assert e.value.status == 6
+    with pytest.raises(pkg.RimoError):
+        splan.build_holographic()
+
+
+def test_surrogate_plan_needs_a_network():
+    import paper_2605_26347_gb300 as pkg
+    uvw = synth.make_uvw(2000, 60, 1.28e9, 95)
+    fov = math.radians(1.0)
+    p = pkg.Plan(uvw, pkg.default_params(64, 64, fov, fov, n_wbins=2, mode=pkg.MODE_SURROGATE))
+    import torch
+    with pytest.raises(pkg.RimoError) as e:
+        p.phi_adj_phi(torch.zeros((64, 64), dtype=torch.complex64, device="cuda"))
+    assert e.value.status == 7
