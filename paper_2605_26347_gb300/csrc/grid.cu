@@ -73,6 +73,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr int GTG_CONSUMERS = 16;                        // consumer warps
 constexpr int GTG_THREADS = (GTG_CONSUMERS + 1) * 32;   // + one producer warp
 constexpr int GTG_NBUF = 4;   // maximum depth of the tap ring (the plan may use fewer)
+constexpr int GTG_HDR = 256;  // shared-memory header: the ring's and the X buffers' mbarriers
 constexpr int GTG_CV = 16;    // visibilities per chunk (one per consumer warp when de-gridding)
 
 struct GtgArgs {
@@ -93,6 +94,7 @@ struct GtgArgs {
     const uint32_t* fx;     // fixed-point bounds (tap bounds; maxterm of a Phi^dagger apply)
     const uint8_t* need;    // [tile] of this bin: some footprint reaches the tile
     int ntv, shift;
+    int prefetch;           // the producer bulk-copies the next unit's X patch (double buffer)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -149,7 +151,9 @@ __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const flo
     const int k = lane & 1;
     const int c = (lane % (2 * CW)) >> 1;
     const int roff = lane / (2 * CW);
-    const float2* Tl = T + roff * S + c;
+    // lane k reads its tap as (component k, component 1 - k): no select on the pair
+    const float* Tl = reinterpret_cast<const float*>(T + roff * S + c) + k;
+    const int tsw = 1 - 2 * k;  // offset of the other component
     const int xl = pbase + roff * PW + c;
     float2 ab[KEEP ? NI : 1][KEEP ? NCG : 1];
     float acc1 = 0.f, acc2 = 0.f;
@@ -158,8 +162,8 @@ __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const flo
 #pragma unroll
         for (int j = 0; j < NCG; ++j) {
             const bool ok = (i * RPI + roff < S) && (c + j * CW < S);
-            float2 t = ok ? Tl[i * RPI * S + j * CW] : make_float2(0.f, 0.f);
-            const float2 e = make_float2(k ? t.y : t.x, k ? t.x : t.y);
+            const float* tp = Tl + 2 * (i * RPI * S + j * CW);
+            const float2 e = ok ? make_float2(tp[0], tp[tsw]) : make_float2(0.f, 0.f);
             if (KEEP) ab[KEEP ? i : 0][KEEP ? j : 0] = e;
             if (GATHER && ok) {
                 const float2 x = Xs[xl + i * RPI * PW + j * CW];
@@ -192,8 +196,8 @@ __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const flo
                     if (KEEP) {
                         e = ab[KEEP ? i : 0][KEEP ? j : 0];
                     } else {
-                        const float2 t = Tl[i * RPI * S + j * CW];
-                        e = make_float2(k ? t.y : t.x, k ? t.x : t.y);
+                        const float* tp = Tl + 2 * (i * RPI * S + j * CW);
+                        e = make_float2(tp[0], tp[tsw]);
                     }
                     // scaled contribution, |d| <= 2^21, split into rint(d) and 2^16 x residual
                     const float d = fmaf(e.x, ysx, e.y * yys);
@@ -242,13 +246,17 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
     uint64_t* empty = full + GTG_NBUF;
-    VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + 128);          // GTG_NBUF x 16 entries
-    float2* taps = reinterpret_cast<float2*>(smraw + 128 + GTG_NBUF * GTG_CV * sizeof(VisMeta));
+    uint64_t* xfull = empty + GTG_NBUF;  // [2] X patch buffer landed
+    uint64_t* xfree = xfull + 2;         // [2] consumers are done with the buffer
+    VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + GTG_HDR);      // GTG_NBUF x 16 entries
+    float2* taps = reinterpret_cast<float2*>(smraw + GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta));
     const int PW = A.PW, npatch = PW * PW;
     const int chunk_f2 = A.chunk_bytes / 8;
     const uint32_t NB = (uint32_t)A.nbuf;
-    float2* Xs = taps + (size_t)NB * chunk_f2;
-    int* Ahi = reinterpret_cast<int*>(Xs + (GATHER ? npatch : 0));  // [cell][re, im] words
+    const bool pre = GATHER && A.prefetch;
+    float2* Xbuf0 = taps + (size_t)NB * chunk_f2;
+    float2* Xbuf1 = Xbuf0 + (pre ? npatch : 0);
+    int* Ahi = reinterpret_cast<int*>(Xbuf1 + (GATHER ? npatch : 0));  // [cell][re, im] words
     int* Alo = Ahi + (SCATTER ? 2 * npatch : 0);
     __shared__ volatile int s_abort;
     __shared__ float s_xmax[GTG_CONSUMERS];
@@ -259,6 +267,10 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         for (int b = 0; b < GTG_NBUF; ++b) {
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], GTG_CONSUMERS);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&xfull[b], 1);
+            mbar_init(&xfree[b], GTG_CONSUMERS);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -274,6 +286,32 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
             if (idx >= A.nunits) break;
             const TileDesc td = A.units[A.sched[idx]];
             const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
+            if (pre) {
+                // X patch of this unit into buffer r & 1, once the consumers released it
+                // (unit r - 2); rows wrap along u, a row past the last column splits in two
+                const int j = r & 1;
+                if (r >= 2 && !s_abort && !mbar_wait_bounded(&xfree[j], ((r >> 1) - 1) & 1)) {
+                    s_abort = 1;
+                    atomicExch(A.status, 1);
+                }
+                if (s_abort) {
+                    for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
+                        (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
+                    if (r >= 1) (void)mbar_wait_bounded(&xfull[(r - 1) & 1], ((r - 1) >> 1) & 1);
+                    return;
+                }
+                float2* dst = j ? Xbuf1 : Xbuf0;
+                const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
+                const int n1 = (v0 + PW <= A.gy) ? PW : A.gy - v0;  // cells before the wrap
+                mbar_arrive_expect_tx(&xfull[j], (uint32_t)(npatch * sizeof(float2)));
+                for (int a = 0; a < PW; ++a) {
+                    int gu = u0 + a;
+                    if (gu >= A.gx) gu -= A.gx;
+                    const float2* row = A.X + (size_t)gu * A.gy;
+                    bulk_g2s(dst + a * PW, row + v0, (uint32_t)(n1 * sizeof(float2)), &xfull[j]);
+                    if (n1 < PW) bulk_g2s(dst + a * PW + n1, row, (uint32_t)((PW - n1) * sizeof(float2)), &xfull[j]);
+                }
+            }
             for (int c = 0; c < nchunks; ++c, ++g) {
                 const ChunkDesc cd = A.chunks[td.cb + c];
                 const int64_t v0 = td.vb + (int64_t)c * GTG_CV;
@@ -287,6 +325,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                     // let the copies already in flight land before the block may exit
                     for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
                         (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
+                    if (pre) (void)mbar_wait_bounded(&xfull[r & 1], (r >> 1) & 1);
                     return;
                 }
                 mbar_arrive_expect_tx(&full[b], cd.bytes + nv * (uint32_t)sizeof(VisMeta));
@@ -307,18 +346,30 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
         float xm = 0.f;
+        float2* Xs = (r & 1) && pre ? Xbuf1 : Xbuf0;
+        if (pre && !s_abort && !mbar_wait_bounded(&xfull[r & 1], (r >> 1) & 1)) {
+            s_abort = 1;
+            atomicExch(A.status, 1);
+        }
         for (int a = warp; a < PW; a += GTG_CONSUMERS) {
             int gu = u0 + a;
             if (gu >= A.gx) gu -= A.gx;
             for (int b = lane; b < PW; b += 32) {
                 if (GATHER) {
-                    int gv = v0 + b;
-                    if (gv >= A.gy) gv -= A.gy;
-                    // cells of tiles no footprint reaches hold no grid values of this bin
-                    const float2 x = A.need[(gu >> A.shift) * A.ntv + (gv >> A.shift)]
-                                         ? A.X[(size_t)gu * A.gy + gv] : make_float2(0.f, 0.f);
-                    Xs[a * PW + b] = x;
-                    xm = fmaxf(xm, fabsf(x.x) + fabsf(x.y));
+                    float2 x;
+                    if (pre) {
+                        x = Xs[a * PW + b];  // landed by the producer (cells outside the bin's
+                                             // footprints hold finite values of other bins)
+                    } else {
+                        int gv = v0 + b;
+                        if (gv >= A.gy) gv -= A.gy;
+                        // cells of tiles no footprint reaches hold no grid values of this bin
+                        x = A.need[(gu >> A.shift) * A.ntv + (gv >> A.shift)] ? A.X[(size_t)gu * A.gy + gv]
+                                                                              : make_float2(0.f, 0.f);
+                        Xs[a * PW + b] = x;
+                    }
+                    const float m = fabsf(x.x) + fabsf(x.y);
+                    if (m <= 3.4028234e38f) xm = fmaxf(xm, m);  // non-finite input is flagged elsewhere
                 }
                 if (SCATTER) {
                     reinterpret_cast<int2*>(Ahi)[a * PW + b] = make_int2(0, 0);
@@ -362,6 +413,10 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
         }
+        if (pre) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xfree[r & 1]);
+        }
         consumers_sync();
         if (SCATTER && !s_abort) {
             float2* dst = A.patch + (size_t)slot * npatch;
@@ -392,11 +447,12 @@ __global__ void __launch_bounds__(256) merge_patches_kernel(float2* __restrict__
     }
 }
 
-size_t gtg_smem(const rimo_plan* p, int mode, int nbuf) {
+size_t gtg_smem(const rimo_plan* p, int mode, int nbuf, bool prefetch) {
     const size_t npatch = (size_t)p->PW * p->PW * sizeof(float2);
-    // X patch (float2) when de-gridding, hi + lo words (2 x int2) when gridding
-    return 128 + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * p->chunk_bytes +
-           (size_t)((mode != 1 ? 1 : 0) + (mode != 0 ? 2 : 0)) * npatch;
+    // X patch (float2; two when prefetched) when de-gridding, hi + lo words (2 x int2) when gridding
+    const int nx = mode != 1 ? (prefetch ? 2 : 1) : 0;
+    return GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * p->chunk_bytes +
+           (size_t)(nx + (mode != 0 ? 2 : 0)) * npatch;
 }
 
 template <int MODE>
@@ -426,9 +482,11 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.shift = p->TS == 64 ? 6 : 5;
     A.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * A.ntv;
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
+    // prefetch the X patches when a double buffer still leaves a 4-deep tap ring
+    A.prefetch = MODE != 1 && gtg_smem(p, MODE, 4, true) <= limit;
     A.nbuf = GTG_NBUF;
-    while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf) > limit) --A.nbuf;
-    const size_t sm = gtg_smem(p, MODE, A.nbuf);
+    while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf, A.prefetch) > limit) --A.nbuf;
+    const size_t sm = gtg_smem(p, MODE, A.nbuf, A.prefetch);
     if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
     RIMO_CUDA(cudaFuncSetAttribute(gtg_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nu, p->n_sm);

@@ -520,6 +520,9 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->d_gblock_ptrs = upload(p, ptrs, s);
     const size_t grid_elems = (size_t)gx * gy;
     p->d_X = (float2*)dev_alloc(p, grid_elems * sizeof(float2));
+    // every cell finite from the start: the gridding step may stage cells that no footprint
+    // of the current bin reaches
+    RIMO_CUDA(cudaMemsetAsync(p->d_X, 0, grid_elems * sizeof(float2), s));
     p->d_slot = upload(p, slot, s);
     {
         // tiles of X read by the patch of some active tile: the tile itself and its
