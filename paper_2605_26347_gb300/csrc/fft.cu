@@ -164,27 +164,34 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
     }
 }
 
-// Radix plan: 16, 16, ..., then the remainder (2, 4, 8 or 16).
+// Radix plan of an L-point transform: 16, then 16s, then the remainder; L <= 256: two
+// stages (16, L/16), L <= 4096: three (16, 16, L/256), L = 8192: four (16, 16, 16, 2).
 template <int N>
 struct Plan16 {
-    static constexpr int R_LAST = (N == 64) ? 4 : (N == 128) ? 8 : (N == 256) ? 16
-                                : (N == 512) ? 2 : (N == 1024) ? 4 : (N == 2048) ? 8 : 16;
+    static constexpr int STAGES = N <= 256 ? 2 : (N <= 4096 ? 3 : 4);
+    static constexpr int R_LAST = N <= 256 ? N / 16 : (N <= 4096 ? N / 256 : N / 4096);
 };
 
 // In: v[m] = element t + T m of the input.  Out: element t + T m of the output is
 // v[out_slot<N>(m)].  All threads of the block must call it (block-wide barriers).
 // tws: the stage twiddle tables of length N (see stage_twiddles on the host): the second
-// stage's W_{16 R}^{r j} at [0, 16 R), the third stage's W_{256 R}^{r j} at [256, 256 + 256 R).
+// stage's W_{16 R}^{r j} at [0, 16 R), the third stage's W_{256 R}^{r j} at [256, 256 + 256 R),
+// a fourth stage's W_{4096 R}^{r j} at [4352, 4352 + 4096 R).
 template <int N, bool INV>
 __device__ __forceinline__ void fft_n(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tws) {
     constexpr int RL = Plan16<N>::R_LAST;
-    if constexpr (N == 64 || N == 128 || N == 256) {
+    if constexpr (Plan16<N>::STAGES == 2) {
         fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
         fft_stage<N, RL, 16, INV, false, true>(v, sm, t, tws);
-    } else {
+    } else if constexpr (Plan16<N>::STAGES == 3) {
         fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
         fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tws);
         fft_stage<N, RL, 256, INV, false, true>(v, sm, t, tws + 256);
+    } else {
+        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tws);
+        fft_stage<N, 16, 256, INV, false, false>(v, sm, t, tws + 256);
+        fft_stage<N, RL, 4096, INV, false, true>(v, sm, t, tws + 256 + 4096);
     }
 }
 
@@ -308,108 +315,121 @@ __device__ __forceinline__ float2 dsmem_ld2(uint32_t addr) {
     return v;
 }
 
+// The oversampled transforms: one L = 2N point transform per row (16 values per thread,
+// T = L/16 = N/8 threads).  Forward: the centred N samples (c = j - N/2 in [-N/2, N/2)) sit
+// at positions c mod L of the zero-padded input, i.e. thread slots m < 4 (c = t + T m) and
+// m >= 12 (c = t + T m - L); the other slots are zero.  Inverse: of the L outputs only
+// c mod L with c in [-N/2, N/2) (the crop) are kept.
+
+// Transposed store of a CTA's (C = 1) or a cluster's (C > 1) rows: output row dst(kk) of
+// `out` (leading dimension ld) gets, at columns [r0, r0 + C RB), value src(kk) of each of
+// the C RB rows, for the nk kept values kk.  With C > 1, after a cluster barrier each CTA
+// writes nk / C of them for all the cluster's rows, reading partners' rows through
+// distributed shared memory (64-byte writes for C RB = 8).
+template <int RB, int C, int SR, int NK, int THREADS, class Src, class Dst>
+__device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst, float2* out, size_t ld,
+                                                 int r0_block) {
+    if constexpr (C == 1) {
+        __syncthreads();
+        constexpr int NP = RB / 2;
+        for (int e = threadIdx.x; e < NK * NP; e += THREADS) {
+            const int kk = e / NP, q = e % NP;
+            const int k = src(kk);
+            const float2 a = smem[(2 * q) * SR + pidx(k)], b = smem[(2 * q + 1) * SR + pidx(k)];
+            *reinterpret_cast<float4*>(&out[(size_t)dst(kk) * ld + r0_block + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
+        }
+        __syncthreads();
+    } else {
+        cluster_sync_all();
+        constexpr int NP = C * RB / 2, KPC = NK / C;
+        static_assert(THREADS % NP == 0, "a thread keeps one row pair");
+        const int rank = (int)(blockIdx.x % C);
+        const int rbase = (int)(blockIdx.x - rank) * RB;  // first row of the cluster
+        const int q = threadIdx.x % NP;                   // rows 2q, 2q + 1 of the cluster
+        const uint32_t b0 = dsmem_map(smem + ((2 * q) % RB) * SR, (2 * q) / RB);
+        const uint32_t b1 = dsmem_map(smem + ((2 * q + 1) % RB) * SR, (2 * q + 1) / RB);
+        for (int e = threadIdx.x; e < KPC * NP; e += THREADS) {
+            const int kk = rank * KPC + e / NP;
+            const uint32_t off = (uint32_t)pidx(src(kk)) * 8u;
+            const float2 a = dsmem_ld2(b0 + off), b = dsmem_ld2(b1 + off);
+            *reinterpret_cast<float4*>(&out[(size_t)dst(kk) * ld + rbase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
+        }
+        cluster_sync_all();  // partners are done reading before the block may exit
+    }
+}
+
 // ----------------------------------------------------------------------------- forward rows
-// grid: ny / RB blocks of RB * N/16 threads; block b transforms image rows [b RB, b RB + RB).
+// grid: ny / RB blocks of RB * N/8 threads; block b transforms image rows [b RB, b RB + RB):
+// Z_p times the row, zero-padded to 2N, DFT along l; row i of the result is column i of
+// At (At[k][i], k < 2N).
 template <int N, int RB, int C>
-__global__ void __launch_bounds__(RB * N / 16, (1024 / (RB * N / 16)) > 0 ? (1024 / (RB * N / 16)) : 1) fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At,
-                                                                int ny, ZArgs z, const float2* __restrict__ tw2N,
-                                                                const float2* __restrict__ tws) {
-    constexpr int T = N / 16;
+__global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
+    fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At, int ny, ZArgs z,
+                    const float2* __restrict__ tws) {
+    constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
-    float2* sm = smem + g * (N + N / 16);
+    float2* sm = smem + g * SR;
     const int i = blockIdx.x * RB + g;
     const int ic = i - ny / 2;
     const float2* xr = x + (size_t)i * N;
     float2 v[16];
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int ip = t + T * m;
-            const int j = (ip + N / 2) & (N - 1);
-            const int jc = ip < N / 2 ? ip : ip - N;
-            float2 val = cmul(__ldg(&xr[j]), z_factor(z, i, j, ic, jc));
-            if (r) val = cmul(val, __ldg(&tw2N[jc & (2 * N - 1)]));
-            v[m] = val;
-        }
-        fft_n<N, false>(v, sm, t, tws);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
-        if constexpr (C == 1) {
-            __syncthreads();
-            // transposed store: At[(2k + r) * ny + i0 + g'] for the RB rows, RB/2 float4 per k
-            const int i0 = blockIdx.x * RB;
-            for (int e = threadIdx.x; e < N * (RB / 2); e += blockDim.x) {
-                const int k = e / (RB / 2), gp = (e % (RB / 2)) * 2;
-                float2 a = smem[gp * (N + N / 16) + pidx(k)];
-                float2 b = smem[(gp + 1) * (N + N / 16) + pidx(k)];
-                *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + i0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
-            }
-            __syncthreads();
+    for (int m = 0; m < 16; ++m) {
+        if (m >= 4 && m < 12) {
+            v[m] = make_float2(0.f, 0.f);
         } else {
-            // cluster-wide transposed store: this CTA writes k in [rank N / C, (rank + 1) N / C)
-            // for the C x RB rows of the cluster; thread pair slot q (fixed per thread) holds
-            // rows 2q, 2q + 1 of the cluster, which live in CTA 2q / RB
-            cluster_sync_all();
-            constexpr int NP = C * RB / 2, KPC = N / C;
-            const int rank = (int)(blockIdx.x % C);
-            const int ibase = (int)(blockIdx.x - rank) * RB;
-            const int q = threadIdx.x % NP;
-            const int src = (2 * q) / RB, gp = (2 * q) % RB;
-            const uint32_t b0 = dsmem_map(smem + gp * (N + N / 16), src);
-            const uint32_t b1 = dsmem_map(smem + (gp + 1) * (N + N / 16), src);
-            for (int e = threadIdx.x; e < KPC * NP; e += blockDim.x) {
-                const int k = rank * KPC + e / NP;
-                const float2 a = dsmem_ld2(b0 + (uint32_t)pidx(k) * 8u);
-                const float2 b = dsmem_ld2(b1 + (uint32_t)pidx(k) * 8u);
-                *reinterpret_cast<float4*>(&At[(size_t)(2 * k + r) * ny + ibase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
-            }
-            cluster_sync_all();  // partners are done reading before the rows are reused
+            const int p = t + T * m;
+            const int jc = m < 4 ? p : p - L;
+            const int j = jc + N / 2;
+            v[m] = cmul(__ldg(&xr[j]), z_factor(z, i, j, ic, jc));
         }
     }
+    fft_n<L, false>(v, sm, t, tws);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<L>(m)];
+    transposed_store<RB, C, SR, L, RB * N / 8>(smem, [](int kk) { return kk; }, [](int kk) { return kk; }, At,
+                                               (size_t)ny, (int)blockIdx.x * RB);
 }
 
 // ----------------------------------------------------------------------------- forward cols
-// grid: rows / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
+// grid: gx / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
 // need[tu * ntv + tv] != 0 marks the tiles of X some active patch reads; the rest of X is
-// never read and not stored.  The RG rows of a block lie in one tile row.
+// never read and not stored.
 template <int N, int RG>
-__global__ void __launch_bounds__(RG * N / 16, (768 / (RG * N / 16)) > 0 ? (768 / (RG * N / 16)) : 1) fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X,
-                                                                const uint8_t* __restrict__ need, int shift,
-                                                                const float2* __restrict__ tw2N,
-                                                                const float2* __restrict__ tws) {
-    constexpr int T = N / 16;
+__global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
+    fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X, const uint8_t* __restrict__ need,
+                    int shift, const float2* __restrict__ tws) {
+    constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
-    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RG * (N + N / 16));
+    const int ntv = L >> shift;
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RG * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
-    float2* sm = smem + g * (N + N / 16);
+    float2* sm = smem + g * SR;
     const size_t u = (size_t)blockIdx.x * RG + g;
     const float2* in = At + u * N;
-    float2* out = X + u * (2 * N);
-    {
-        const int ntv = (2 * N) >> shift;
-        const uint8_t* nr = need + (size_t)(((size_t)blockIdx.x * RG) >> shift) * ntv;
-        for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = nr[e];
+    float2* out = X + u * L;
+    for (int e = threadIdx.x; e < RG * ntv; e += blockDim.x) {
+        const size_t uu = (size_t)blockIdx.x * RG + e / ntv;
+        s_need[e] = need[(uu >> shift) * ntv + e % ntv];
+    }
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (m >= 4 && m < 12) {
+            v[m] = make_float2(0.f, 0.f);
+        } else {
+            const int p = t + T * m;
+            const int jc = m < 4 ? p : p - L;
+            v[m] = __ldg(&in[jc + N / 2]);
+        }
     }
     __syncthreads();
-    float2 v[16];
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
+    fft_n<L, false>(v, sm, t, tws);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int ip = t + T * m;
-            const int ic = ip < N / 2 ? ip : ip - N;
-            float2 val = __ldg(&in[(ip + N / 2) & (N - 1)]);
-            if (r) val = cmul(val, __ldg(&tw2N[ic & (2 * N - 1)]));
-            v[m] = val;
-        }
-        fft_n<N, false>(v, sm, t, tws);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int vv = 2 * (t + T * m) + r;
-            if (s_need[vv >> shift]) out[vv] = v[out_slot<N>(m)];
-        }
+    for (int m = 0; m < 16; ++m) {
+        const int k = t + T * m;
+        if (s_need[g * ntv + (k >> shift)]) out[k] = v[out_slot<L>(m)];
     }
 }
 
@@ -446,118 +466,67 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs F) {
 
 // ----------------------------------------------------------------------------- inverse cols
 // grid: gx / RB blocks; rows u of Xh (2N cells along v; cells of tiles without a mark in
-// need[] are zero and not read) -> B[i][u] for the N image rows.  The RB rows of a block
-// lie in one tile row (RB <= TS).
+// need[] are zero and not read) -> B[i][u] for the N image rows i.
 template <int N, int RB, int C>
-__global__ void __launch_bounds__(RB * N / 16, (RB * N / 16) <= 512 ? 2 : 1) inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B,
-                                                                int gx, const uint8_t* __restrict__ need, int shift,
-                                                                const float2* __restrict__ tw2N,
-                                                                const float2* __restrict__ tws) {
-    constexpr int T = N / 16;
+__global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
+    inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B, int gx, const uint8_t* __restrict__ need,
+                    int shift, const float2* __restrict__ tws) {
+    constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
-    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RB * (N + N / 16));
+    const int ntv = L >> shift;
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RB * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
-    float2* sm = smem + g * (N + N / 16);
+    float2* sm = smem + g * SR;
     const int u = blockIdx.x * RB + g;
-    {
-        const int ntv = (2 * N) >> shift;
-        const uint8_t* nr = need + (size_t)((blockIdx.x * RB) >> shift) * ntv;
-        for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = nr[e];
+    for (int e = threadIdx.x; e < RB * ntv; e += blockDim.x) {
+        const int uu = blockIdx.x * RB + e / ntv;
+        s_need[e] = need[(size_t)(uu >> shift) * ntv + e % ntv];
     }
     __syncthreads();
-    const float2* in = Xh + (size_t)u * (2 * N);
+    const float2* in = Xh + (size_t)u * L;
     float2 v[16];
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int k = t + T * m;
-            const float2 a = s_need[k >> shift] ? __ldg(&in[k]) : make_float2(0.f, 0.f);
-            const float2 b = s_need[(k + N) >> shift] ? __ldg(&in[k + N]) : make_float2(0.f, 0.f);
-            v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
-        }
-        fft_n<N, true>(v, sm, t, tws);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<N>(m)];
-        // keep outputs m' in [0, N/4) u [3N/4, N): image row i = 2 mm + r + N/2
-        if constexpr (C == 1) {
-            __syncthreads();
-            const int u0 = blockIdx.x * RB;
-            for (int e = threadIdx.x; e < (N / 2) * (RB / 2); e += blockDim.x) {
-                const int kk = e / (RB / 2), gp = (e % (RB / 2)) * 2;
-                const int mp = kk < N / 4 ? kk : kk + N / 2;
-                const int mm = kk < N / 4 ? kk : kk - N / 2;
-                const int i = 2 * mm + r + N / 2;
-                float2 a = smem[gp * (N + N / 16) + pidx(mp)];
-                float2 b = smem[(gp + 1) * (N + N / 16) + pidx(mp)];
-                *reinterpret_cast<float4*>(&B[(size_t)i * gx + u0 + gp]) = make_float4(a.x, a.y, b.x, b.y);
-            }
-            __syncthreads();
-        } else {
-            // cluster-wide transposed store (see fwd_rows_kernel): this CTA writes outputs kk in
-            // [rank N / (2C), (rank + 1) N / (2C)) for the C x RB grid rows u of the cluster
-            cluster_sync_all();
-            constexpr int NP = C * RB / 2, KPC = (N / 2) / C;
-            const int rank = (int)(blockIdx.x % C);
-            const int ubase = (int)(blockIdx.x - rank) * RB;
-            const int q = threadIdx.x % NP;
-            const int src = (2 * q) / RB, gp = (2 * q) % RB;
-            const uint32_t b0 = dsmem_map(smem + gp * (N + N / 16), src);
-            const uint32_t b1 = dsmem_map(smem + (gp + 1) * (N + N / 16), src);
-            for (int e = threadIdx.x; e < KPC * NP; e += blockDim.x) {
-                const int kk = rank * KPC + e / NP;
-                const int mp = kk < N / 4 ? kk : kk + N / 2;
-                const int mm = kk < N / 4 ? kk : kk - N / 2;
-                const int i = 2 * mm + r + N / 2;
-                const float2 a = dsmem_ld2(b0 + (uint32_t)pidx(mp) * 8u);
-                const float2 b = dsmem_ld2(b1 + (uint32_t)pidx(mp) * 8u);
-                *reinterpret_cast<float4*>(&B[(size_t)i * gx + ubase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
-            }
-            cluster_sync_all();
-        }
+    for (int m = 0; m < 16; ++m) {
+        const int p = t + T * m;
+        v[m] = s_need[g * ntv + (p >> shift)] ? __ldg(&in[p]) : make_float2(0.f, 0.f);
     }
+    fft_n<L, true>(v, sm, t, tws);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<L>(m)];
+    // kept output kk < N: k = kk (kk < N/2) or kk + N; image row i = (k < N/2 ? k : k - L) + N/2
+    transposed_store<RB, C, SR, N, RB * N / 8>(
+        smem, [](int kk) { return kk < N / 2 ? kk : kk + N; },
+        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, B, (size_t)gx, (int)blockIdx.x * RB);
 }
 
 // ----------------------------------------------------------------------------- inverse rows
 // grid: ny / RG blocks; row i of B (2N cells along u) -> out[i][0 .. N) * conj(Z_p)
 template <int N, int RG>
-__global__ void __launch_bounds__(RG * N / 16, (768 / (RG * N / 16)) > 0 ? (768 / (RG * N / 16)) : 1) inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out,
-                                                                int ny, ZArgs z, int accumulate, int real_only,
-                                                                const float2* __restrict__ tw2N,
-                                                                const float2* __restrict__ tws) {
-    constexpr int T = N / 16;
+__global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
+    inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out, int ny, ZArgs z, int accumulate,
+                    int real_only, const float2* __restrict__ tws) {
+    constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
-    float2* sm = smem + g * (N + N / 16);
+    float2* sm = smem + g * SR;
     const int i = blockIdx.x * RG + g;
     const int ic = i - ny / 2;
-    const float2* in = B + (size_t)i * (2 * N);
+    const float2* in = B + (size_t)i * L;
     float2* orow = out + (size_t)i * N;
     float2 v[16];
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int k = t + T * m;
-            float2 a = __ldg(&in[k]), b = __ldg(&in[k + N]);
-            v[m] = r ? cmulc(csub(a, b), __ldg(&tw2N[k])) : cadd(a, b);
-        }
-        fft_n<N, true>(v, sm, t, tws);
+    for (int m = 0; m < 16; ++m) v[m] = __ldg(&in[t + T * m]);
+    fft_n<L, true>(v, sm, t, tws);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int mp = t + T * m;
-            if (mp >= N / 4 && mp < 3 * N / 4) continue;
-            const int mm = mp < N / 4 ? mp : mp - N;
-            const int jc = 2 * mm + r;
-            const int j = jc + N / 2;
-            float2 val = cmulc(v[out_slot<N>(m)], z_factor(z, i, j, ic, jc));
-            if (accumulate) {
-                float2 o = orow[j];
-                val = cadd(val, o);
-            }
-            if (real_only) val.y = 0.f;
-            orow[j] = val;
-        }
+    for (int m = 0; m < 16; ++m) {
+        const int k = t + T * m;
+        if (k >= N / 2 && k < 3 * N / 2) continue;  // outside the crop
+        const int jc = k < N / 2 ? k : k - L;
+        const int j = jc + N / 2;
+        float2 val = cmulc(v[out_slot<L>(m)], z_factor(z, i, j, ic, jc));
+        if (accumulate) val = cadd(val, orow[j]);
+        if (real_only) val.y = 0.f;
+        orow[j] = val;
     }
 }
 
@@ -580,14 +549,9 @@ void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s) {
     image_bound_kernel<<<blocks, 256, 0, s>>>(x, p->nx, p->ny, zargs(p, 0), p->d_fx, p->d_status);
 }
 
+// rows per block of the 2N-point passes: 512 threads (N / 8 per row), ~70 KB of shared memory
 template <int N>
-static constexpr int rows_per_block() { return (N / 16) >= 256 ? 2 : (N / 16) >= 64 ? 4 : 256 / (N / 16); }
-// the inverse cols pass sums up to four patches per input point: fewer rows per block
-// leave it the registers to keep them in flight
-template <int N>
-static constexpr int inv_rows_per_block() { return (N / 16) >= 256 ? 2 : rows_per_block<N>(); }
-template <int N>
-static constexpr int groups_per_block() { return (N / 16) >= 256 ? 1 : 256 / (N / 16); }
+static constexpr int rows_per_block() { return 4096 / N; }
 // CTAs per cluster of the transposed-store passes: 8 rows per cluster (64-byte writes)
 template <int RB>
 static constexpr int cluster_of() { return RB >= 8 ? 1 : 8 / RB; }
@@ -641,35 +605,37 @@ template <int N>
 static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
     constexpr int RB = rows_per_block<N>();
     constexpr int C = cluster_of<RB>();
-    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2);
+    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2);
     const int grid = p->ny / RB;
-    if (C > 1 && grid % C == 0) {
+    if constexpr (C > 1) {
+        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "image rows do not fill the transposed-store clusters");
         set_smem(fwd_rows_kernel<N, RB, C>, sm);
-        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 16, sm, C, s, x, At, p->ny, zargs(p, bin),
-                         (const float2*)p->tab.tw_x, (const float2*)p->tab.tws_x);
+        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, x, At, p->ny, zargs(p, bin),
+                         (const float2*)p->tab.tws_x);
     } else {
         set_smem(fwd_rows_kernel<N, RB, 1>, sm);
-        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 16, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tw_x, p->tab.tws_x);
+        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tws_x);
     }
 }
 
 template <int N>
 static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
-    constexpr int RG = groups_per_block<N>();
-    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2) + 256;
+    constexpr int RG = rows_per_block<N>();
+    const int ntv = (2 * N) / p->TS;
+    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
     set_smem(fwd_cols_kernel<N, RG>, sm);
     const size_t ntile = (size_t)(p->gx / p->TS) * (p->gy / p->TS);
-    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 16, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
-                                                                p->TS == 64 ? 6 : 5, p->tab.tw_y, p->tab.tws_y);
+    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 8, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
+                                                               p->TS == 64 ? 6 : 5, p->tab.tws_y);
 }
 
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStream_t s) {
-    constexpr int RB = inv_rows_per_block<N>();
+    constexpr int RB = rows_per_block<N>();
     constexpr int C = cluster_of<RB>();
-    const size_t sm = (size_t)RB * (N + N / 16) * sizeof(float2) + 256;
     const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
     const size_t ntile = (size_t)ntu * ntv;
+    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2) + (size_t)RB * ntv + 16;
     const auto& br = p->bins[bin];
     if (br.n1 > br.n0) {
         FoldArgs F;
@@ -689,25 +655,24 @@ static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStre
     }
     const int grid = p->gx / RB, shift = p->TS == 64 ? 6 : 5;
     const uint8_t* need = p->d_need + (size_t)bin * ntile;
-    if (C > 1 && grid % C == 0) {
+    if constexpr (C > 1) {
+        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
         set_smem(inv_cols_kernel<N, RB, C>, sm);
-        launch_clustered(inv_cols_kernel<N, RB, C>, grid, RB * N / 16, sm, C, s, (const float2*)p->d_X, B, p->gx,
-                         need, shift, (const float2*)p->tab.tw_y, (const float2*)p->tab.tws_y);
+        launch_clustered(inv_cols_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, (const float2*)p->d_X, B, p->gx,
+                         need, shift, (const float2*)p->tab.tws_y);
     } else {
         set_smem(inv_cols_kernel<N, RB, 1>, sm);
-        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 16, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tw_y,
-                                                                p->tab.tws_y);
+        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tws_y);
     }
 }
 
 template <int N>
 static void inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int acc, int re,
                      cudaStream_t s) {
-    constexpr int RG = groups_per_block<N>();
-    const size_t sm = (size_t)RG * (N + N / 16) * sizeof(float2);
+    constexpr int RG = rows_per_block<N>();
+    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2);
     set_smem(inv_rows_kernel<N, RG>, sm);
-    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 16, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re,
-                                                                p->tab.tw_x, p->tab.tws_x);
+    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 8, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re, p->tab.tws_x);
 }
 
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {

@@ -77,10 +77,8 @@ struct BinRange {
 
 // Constant tables the kernels read.
 struct DevTables {
-    float2* tw_x = nullptr;    // e^{-2 pi i k / (2 nx)}, k in [0, 2 nx)
-    float2* tw_y = nullptr;    // e^{-2 pi i k / (2 ny)}
-    float2* tws_x = nullptr;   // Stockham stage twiddle tables for the nx-point transforms
-    float2* tws_y = nullptr;   // ... and the ny-point transforms
+    float2* tws_x = nullptr;   // Stockham stage twiddle tables for the 2 nx-point transforms
+    float2* tws_y = nullptr;   // ... and the 2 ny-point transforms
     float* gc_x = nullptr;     // grid correction 1 / KB_hat, per column
     float* gc_y = nullptr;     // per row
     float2* dn = nullptr;      // (sqrt(1-l^2-m^2)-1) as float pairs, [|i_c|][|j_c|], (ny/2+1) x (nx/2+1)

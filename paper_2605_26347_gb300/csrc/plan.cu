@@ -131,22 +131,16 @@ static void fill_estimate(rimo_plan_info* info, const planner::Choice& ch, int64
 // Device tables of one plan.
 static void build_tables(rimo_plan* p, cudaStream_t s) {
     const int nx = p->nx, ny = p->ny, J = p->J, L = p->L;
-    auto twiddles = [](int N) {
-        std::vector<float2> t(2 * N);
-        for (int k = 0; k < 2 * N; ++k) {
-            double a = -2.0 * M_PI * (double)k / (2.0 * N);
-            t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-        return t;
-    };
-    p->tab.tw_x = upload(p, twiddles(nx), s);
-    p->tab.tw_y = upload(p, twiddles(ny), s);
+
     // Stockham stage tables: stage 2 combines NS = 16 points with radix R2, stage 3
     // NS = 256 with radix R3; entry [r NS + j] = W_{NS R}^{r j} = e^{-2 pi i r j / (NS R)}
+    // stage twiddle tables of the L-point transforms (L = 2 n): stages 16 (NS 16),
+    // 16 or L/256 (NS 256), L/4096 (NS 4096), laid out [r][j]
     auto stage_twiddles = [](int N) {
         const int R2 = N <= 256 ? N / 16 : 16;
-        const int R3 = N <= 256 ? 0 : N / 256;
-        std::vector<float2> t((size_t)std::max(N, 256 + 256 * std::max(R3, 1)), make_float2(0.f, 0.f));
+        const int R3 = N <= 256 ? 0 : (N <= 4096 ? N / 256 : 16);
+        const int R4 = N <= 4096 ? 0 : N / 4096;
+        std::vector<float2> t((size_t)std::max(N, 256 + 256 * std::max(R3, 1) + 4096 * R4), make_float2(0.f, 0.f));
         auto fill = [&](size_t off, int NS, int R) {
             for (int r = 0; r < R; ++r)
                 for (int j = 0; j < NS; ++j) {
@@ -156,10 +150,11 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
         };
         fill(0, 16, R2);
         if (R3) fill(256, 256, R3);
+        if (R4) fill(256 + 4096, 4096, R4);
         return t;
     };
-    p->tab.tws_x = upload(p, stage_twiddles(nx), s);
-    p->tab.tws_y = upload(p, stage_twiddles(ny), s);
+    p->tab.tws_x = upload(p, stage_twiddles(2 * nx), s);
+    p->tab.tws_y = upload(p, stage_twiddles(2 * ny), s);
     auto gc = [&](int n) {
         std::vector<float> g(n);
         for (int j = 0; j < n; ++j) g[j] = (float)(1.0 / kb_hat((double)(j - n / 2) / (2.0 * n), J, p->beta));
