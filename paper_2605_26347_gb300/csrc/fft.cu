@@ -218,21 +218,19 @@ __device__ __forceinline__ float2 wphase(float w_hi, float w_lo, float2 d) {
 }
 
 struct ZArgs {
-    const float2* dn;   // quarter table [|i_c|][|j_c|]
-    int dn_ld;
-    const float* gcx;
-    const float* gcy;
+    const float4* zq;   // quarter table [|i_c|][|j_c|]: (n - 1) as a float pair, |Z_p|
+    int zq_ld;
     float w_hi, w_lo;
-    int div_n;
 };
 
-// Z_p(i, j) = gc_x[j] gc_y[i] e^{-2 pi i w dn(l_j, m_i)} [/ (1 + dn)]
+// Z_p(i, j) = gc_x gc_y [/ n] e^{-2 pi i w (n - 1)} at (l_j, m_i): one table load (the grid
+// correction and the w-term depend on |i_c|, |j_c| only)
 __device__ __forceinline__ float2 z_factor(const ZArgs& z, int i, int j, int ic, int jc) {
-    float2 d = __ldg(&z.dn[abs(ic) * z.dn_ld + abs(jc)]);
-    float2 ph = wphase(z.w_hi, z.w_lo, d);
-    float g = __ldg(&z.gcx[j]) * __ldg(&z.gcy[i]);
-    if (z.div_n) g = g / (1.0f + (d.x + d.y));
-    return make_float2(ph.x * g, ph.y * g);
+    (void)i;
+    (void)j;
+    const float4 q = __ldg(&z.zq[abs(ic) * z.zq_ld + abs(jc)]);
+    const float2 ph = wphase(z.w_hi, z.w_lo, make_float2(q.x, q.y));
+    return make_float2(ph.x * q.z, ph.y * q.z);
 }
 
 // ----------------------------------------------------------------------------- bound
@@ -252,11 +250,7 @@ __global__ void __launch_bounds__(256) image_bound_kernel(const float2* __restri
     const int n = nx * ny;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int i = e / nx, j = e - i * nx;
-        float g = __ldg(&z.gcx[j]) * __ldg(&z.gcy[i]);
-        if (z.div_n) {
-            const float2 d = __ldg(&z.dn[abs(i - ny / 2) * z.dn_ld + abs(j - nx / 2)]);
-            g = g / (1.0f + (d.x + d.y));
-        }
+        const float g = __ldg(&z.zq[abs(i - ny / 2) * z.zq_ld + abs(j - nx / 2)]).z;  // |Z_p|
         const float2 v = x[e];
         const float m = fabsf(v.x) + fabsf(v.y);
         bad |= !(m <= 3.4028234e38f);
@@ -302,6 +296,10 @@ __global__ void __launch_bounds__(256) image_bound_kernel(const float2* __restri
 // (64 bytes for C x RB = 8) instead of RB x 8.
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// a barrier that orders no memory: all its arrivals' remote reads have returned already
+__device__ __forceinline__ void cluster_sync_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t dsmem_map(const void* ptr, uint32_t rank) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(ptr);
@@ -354,7 +352,7 @@ __device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst,
             const float2 a = dsmem_ld2(b0 + off), b = dsmem_ld2(b1 + off);
             *reinterpret_cast<float4*>(&out[(size_t)dst(kk) * ld + rbase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
         }
-        cluster_sync_all();  // partners are done reading before the block may exit
+        cluster_sync_relaxed();  // partners are done reading before the block may exit
     }
 }
 
@@ -533,13 +531,10 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
 // ----------------------------------------------------------------------------- launchers
 static ZArgs zargs(const rimo_plan* p, int bin) {
     ZArgs z;
-    z.dn = p->tab.dn;
-    z.dn_ld = p->nx / 2 + 1;
-    z.gcx = p->tab.gc_x;
-    z.gcy = p->tab.gc_y;
+    z.zq = p->tab.zq;
+    z.zq_ld = p->nx / 2 + 1;
     z.w_hi = p->bins[bin].w_hi;
     z.w_lo = p->bins[bin].w_lo;
-    z.div_n = p->prm.n_weight == RIMO_NWEIGHT_DIV_N;
     return z;
 }
 

@@ -79,9 +79,7 @@ struct BinRange {
 struct DevTables {
     float2* tws_x = nullptr;   // Stockham stage twiddle tables for the 2 nx-point transforms
     float2* tws_y = nullptr;   // ... and the 2 ny-point transforms
-    float* gc_x = nullptr;     // grid correction 1 / KB_hat, per column
-    float* gc_y = nullptr;     // per row
-    float2* dn = nullptr;      // (sqrt(1-l^2-m^2)-1) as float pairs, [|i_c|][|j_c|], (ny/2+1) x (nx/2+1)
+    float4* zq = nullptr;      // [|i_c|][|j_c|], (ny/2+1) x (nx/2+1): sqrt(1-l^2-m^2)-1 as a float pair, |Z_p|
     float* kb_coef = nullptr;  // Horner coefficients of KB(t) in rho = 1 - (2t/J)^2
     int kb_nterm = 0;
     float* wk_dn = nullptr;    // w-kernel grid: (sqrt(1-lam^2-mu^2)-1), L x L (float)

@@ -155,23 +155,24 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
     };
     p->tab.tws_x = upload(p, stage_twiddles(2 * nx), s);
     p->tab.tws_y = upload(p, stage_twiddles(2 * ny), s);
-    auto gc = [&](int n) {
-        std::vector<float> g(n);
-        for (int j = 0; j < n; ++j) g[j] = (float)(1.0 / kb_hat((double)(j - n / 2) / (2.0 * n), J, p->beta));
-        return g;
-    };
-    p->tab.gc_x = upload(p, gc(nx), s);
-    p->tab.gc_y = upload(p, gc(ny), s);
+    // Z_p on the quarter plane [|i_c|][|j_c|]: (n - 1) as a float pair for the w-phase and
+    // |Z_p| = gc_x gc_y [/ n] (the grid correction is even in j_c and i_c), in FP64 then rounded
     const int qx = nx / 2 + 1, qy = ny / 2 + 1;
-    std::vector<float2> dnq((size_t)qx * qy);
+    std::vector<float4> zq((size_t)qx * qy);
     const double dl = p->prm.fov_x / nx, dm = p->prm.fov_y / ny;
+    std::vector<double> gx_q(qx), gy_q(qy);
+    for (int j = 0; j < qx; ++j) gx_q[j] = 1.0 / kb_hat((double)j / (2.0 * nx), J, p->beta);
+    for (int i = 0; i < qy; ++i) gy_q[i] = 1.0 / kb_hat((double)i / (2.0 * ny), J, p->beta);
+    const bool div_n = p->prm.n_weight == RIMO_NWEIGHT_DIV_N;
     for (int i = 0; i < qy; ++i)
         for (int j = 0; j < qx; ++j) {
-            double d = planner::dn(j * dl, i * dm);
-            float hi = (float)d;
-            dnq[(size_t)i * qx + j] = make_float2(hi, (float)(d - (double)hi));
+            const double d = planner::dn(j * dl, i * dm);
+            const float hi = (float)d;
+            double g = gx_q[j] * gy_q[i];
+            if (div_n) g /= 1.0 + d;
+            zq[(size_t)i * qx + j] = make_float4(hi, (float)(d - (double)hi), (float)g, 0.f);
         }
-    p->tab.dn = upload(p, dnq, s);
+    p->tab.zq = upload(p, zq, s);
     // KB(t) = sum_k e_k rho^k, rho = 1 - (2t/J)^2, e_k = (beta^2/4)^k / (k!)^2 / I0(beta)
     std::vector<float> coef;
     {
