@@ -56,9 +56,10 @@ typedef enum rimo_status {
 typedef enum rimo_mode {
     RIMO_MODE_AUTO = 0,        /* decision tree of Section 3.4 / Fig. 2              */
     RIMO_MODE_STORED_G = 1,    /* precompute and store the de-gridding matrix G      */
-    RIMO_MODE_HOLOGRAPHIC = 2, /* precompute H_p = G_p^dagger G_p (Section 3.3)      */
+    RIMO_MODE_HOLOGRAPHIC = 2, /* H_p = G_p^dagger G_p (Section 3.3) once built; no  */
+                               /* stored G: tiles generated on the fly until then    */
     RIMO_MODE_SURROGATE = 3,   /* kernels generated on the fly by the learned MLP    */
-    RIMO_MODE_ONTHEFLY = 4     /* exact kernels generated on the fly                 */
+    RIMO_MODE_ONTHEFLY = 4     /* exact kernels generated per w-bin at apply time    */
 } rimo_mode;
 
 typedef enum rimo_n_weight {
@@ -214,7 +215,9 @@ rimo_status rimo_apply_phi_adj_phi(rimo_plan_t plan, const rimo_cfloat* x_dev,
 
 /*
  * Build the holographic matrices H_p = G_p^dagger G_p on the device (Section 3.3) and
- * switch rimo_apply_phi_adj_phi (and rimo_psf) to them; Phi and Phi^dagger keep using G.
+ * switch rimo_apply_phi_adj_phi (and rimo_psf) to them; Phi and Phi^dagger keep using the
+ * plan's tiles.  A stored-G plan builds H from G; a holographic or on-the-fly plan generates
+ * each bin's exact tiles for its build, so all of G is never held (Fig. 2, regime b).
  * H_p is Hermitian and stored once per cell pair: every grid cell that some visibility
  * footprint covers gets a row of (H+1)^2 + H^2 complex entries, H = S_max - 1 (421 for
  * S_max = 15), so it pays off where visibilities per covered cell are many.  Fails with

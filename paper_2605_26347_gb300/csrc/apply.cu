@@ -89,6 +89,10 @@ static void gtg(rimo_plan* p, int b, int mode, const float2* y_in, float2* y_out
         prof_begin(p, ST_MLP, s);
         const int nl = surrogate_generate(p, b, s);  // this bin's tiles into the tap scratch
         prof_end(p, nl, s);
+    } else if (p->mode == RIMO_MODE_ONTHEFLY || p->mode == RIMO_MODE_HOLOGRAPHIC) {
+        prof_begin(p, ST_GBUILD, s);
+        launch_gbuild_range(p, p->bins[b].vb, p->bins[b].ve - p->bins[b].vb, s);  // exact tiles
+        prof_end(p, 1, s);
     }
     prof_begin(p, ST_GTG, s);
     launch_gtg(p, b, mode, y_in, y_out, s);
@@ -98,10 +102,9 @@ static void gtg(rimo_plan* p, int b, int mode, const float2* y_in, float2* y_out
 
 static void begin_apply(rimo_plan* p, cudaStream_t s) {
     reset_schedulers(p, s);
-    if (p->mode == RIMO_MODE_SURROGATE) {
-        if (!p->sur) fail(RIMO_ERR_STATE, "surrogate plan without a surrogate (rimo_plan_set_surrogate)");
-        reset_surrogate_bounds(p, s);
-    }
+    if (p->mode == RIMO_MODE_SURROGATE && !p->sur)
+        fail(RIMO_ERR_STATE, "surrogate plan without a surrogate (rimo_plan_set_surrogate)");
+    if (p->mode != RIMO_MODE_STORED_G) reset_surrogate_bounds(p, s);  // tap bounds of generated tiles
 }
 
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s) {

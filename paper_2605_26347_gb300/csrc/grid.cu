@@ -393,7 +393,10 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
             const float mt = 4.f * __uint_as_float(__ldg(A.fx + FX_TMAX)) * __uint_as_float(__ldg(A.fx + FX_T1)) * xmax;
             fx_scale(mt, td.ve - td.vb, s1, inv_s1);
         } else if (SCATTER) {
-            fx_scale(__uint_as_float(__ldg(A.fx + FX_MAXTERM)), td.ve - td.vb, s1, inv_s1);
+            // twice tmax max|y|_1 (rounding margin); both words final before this launch
+            const float mt = 2.f * __uint_as_float(__ldcg(A.fx + FX_TMAX)) * __uint_as_float(__ldcg(A.fx + FX_YB));
+            if (!(mt <= 3.4028234e38f)) atomicExch(A.status, 3);
+            fx_scale(mt, td.ve - td.vb, s1, inv_s1);
         }
         for (int c = 0; c < nchunks; ++c, ++g) {
             const uint32_t b = g % NB, par = (g / NB) & 1;
@@ -503,10 +506,10 @@ void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float
 }
 
 // ---------------------------------------------------------------------------
-// Bound on the grid-step contributions of Phi^dagger y: every contribution component is
-// at most max_taps(|t.x| + |t.y|) * max_k(|y_k.x| + |y_k.y|); twice that (rounding margin)
-// goes to d_fx[FX_MAXTERM].  Non-finite y sets status 3.  The last block to finish
-// (counter in d_fx[FX_COUNT]) writes the bound and resets the running words.
+// Bound on the y of Phi^dagger y: max_k(|y_k.x| + |y_k.y|) goes to d_fx[FX_YB] (a grid-step
+// contribution component is at most that times max_taps(|t.x| + |t.y|)).  Non-finite y
+// sets status 3.  The last block to finish (counter in d_fx[FX_COUNT]) writes the bound and
+// resets the running words.
 __global__ void __launch_bounds__(256) y_bound_kernel(const float2* __restrict__ y, int64_t M, uint32_t* fx,
                                                       int* status) {
     float mx = 0.f;
@@ -528,10 +531,9 @@ __global__ void __launch_bounds__(256) y_bound_kernel(const float2* __restrict__
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        const float ym = __uint_as_float(atomicExch(fx + FX_YMAX, 0u));
-        const float mt = 2.f * __uint_as_float(__ldcg(fx + FX_TMAX)) * ym;
-        if (!(mt <= 3.4028234e38f)) atomicExch(status, 3);
-        fx[FX_MAXTERM] = __float_as_uint(mt);
+        // the gridding step combines it with the tap bound current when it runs (tiles
+        // generated per bin at apply time raise the tap bound bin by bin)
+        fx[FX_YB] = atomicExch(fx + FX_YMAX, 0u);
         fx[FX_COUNT] = 0u;
     }
 }
@@ -564,7 +566,7 @@ struct BuildArgs {
     const float* kb_coef;
     int kb_nterm;
     int L, hmax, J, literal;
-    int64_t nvis;
+    int64_t v0, nvis;        // sorted visibilities [v0, v0 + nvis)
     uint32_t* fx;
 };
 
@@ -605,7 +607,8 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
     const float invL2 = 1.f / ((float)L * (float)L);
     const float invhalf = 2.f / (float)A.J;
     float tmax = 0.f;
-    for (int64_t k = (int64_t)blockIdx.x * BUILD_WARPS + warp; k < A.nvis; k += (int64_t)gridDim.x * BUILD_WARPS) {
+    for (int64_t k = A.v0 + (int64_t)blockIdx.x * BUILD_WARPS + warp; k < A.v0 + A.nvis;
+         k += (int64_t)gridDim.x * BUILD_WARPS) {
         float tsum = 0.f;
         const VisMeta mt = A.meta[k];
         const int S = (mt.pos >> 16) & 255;
@@ -710,8 +713,10 @@ size_t gbuild_smem(int L, int hmax) {
            (size_t)BUILD_WARPS * per_warp * sizeof(float2);
 }
 
-void launch_gbuild(const rimo_plan* p, cudaStream_t s) {
-    if (p->M == 0) return;
+void launch_gbuild(const rimo_plan* p, cudaStream_t s) { launch_gbuild_range(p, 0, p->M, s); }
+
+void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
     BuildArgs A;
     A.meta = p->d_meta;
     A.wr = p->d_wr;
@@ -728,14 +733,15 @@ void launch_gbuild(const rimo_plan* p, cudaStream_t s) {
     A.hmax = p->hmax;
     A.J = p->J;
     A.literal = p->prm.taper_literal != 0;
-    A.nvis = p->M;
+    A.v0 = v0;
+    A.nvis = n;
     A.fx = p->d_fx;
     const size_t sm = gbuild_smem(p->L, p->hmax);
     RIMO_CUDA(cudaFuncSetAttribute(gbuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int dev = 0, nsm = 0;
     RIMO_CUDA(cudaGetDevice(&dev));
     RIMO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int64_t blocks = (p->M + BUILD_WARPS - 1) / BUILD_WARPS;
+    int64_t blocks = (n + BUILD_WARPS - 1) / BUILD_WARPS;
     blocks = std::min<int64_t>(blocks, (int64_t)nsm * 8);
     gbuild_kernel<<<(int)blocks, BUILD_WARPS * 32, sm, s>>>(A);
 }

@@ -597,6 +597,8 @@ static void build_holographic(rimo_plan* p, cudaStream_t s) {
         A.hoff = p->d_hoff[b];
         A.rows = p->d_hrows[b];
         A.tmax = p->d_htmax[b];
+        // without stored G, the bin's exact tiles are generated into the tap scratch first
+        if (p->mode != RIMO_MODE_STORED_G) launch_gbuild_range(p, p->bins[b].vb, p->bins[b].ve - p->bins[b].vb, s);
         hbuild_kernel<<<nneed * per_tile, HB_WARPS * 32, sm, s>>>(A, p->max_S);
         RIMO_CUDA(cudaGetLastError());
     }
@@ -613,7 +615,7 @@ extern "C" {
 rimo_status rimo_build_holographic(rimo_plan_t p, void* stream) {
     RIMO_API_BEGIN
     if (!p) fail(RIMO_ERR_INVALID_ARG, "null plan");
-    if (p->mode == RIMO_MODE_SURROGATE) fail(RIMO_ERR_UNSUPPORTED, "a surrogate plan stores no G to build H from");
+    if (p->mode == RIMO_MODE_SURROGATE) fail(RIMO_ERR_UNSUPPORTED, "H is built from exact tiles");
     if (!p->h_built) build_holographic(p, (cudaStream_t)stream);
     RIMO_API_END
 }

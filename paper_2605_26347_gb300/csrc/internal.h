@@ -107,7 +107,6 @@ struct rimo_plan {
     std::vector<int32_t> sched_host;             // per bin: unit indices, heaviest first
     std::vector<int2> merge_host;                // per bin: (first slot, units) of split tiles
     std::vector<int64_t> block_bytes;
-    bool holographic = false;
 
     // device
     rimo::VisMeta* d_meta = nullptr;
@@ -132,7 +131,8 @@ struct rimo_plan {
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
 
-    // kernel surrogate (mode RIMO_MODE_SURROGATE): tiles generated per bin at apply time
+    // kernel surrogate (mode RIMO_MODE_SURROGATE) or exact on-the-fly tiles (mode
+    // RIMO_MODE_ONTHEFLY): tiles generated per bin at apply time
     struct rimo_surrogate* sur = nullptr;  // attached by rimo_plan_set_surrogate (not owned)
     float2* d_sur_taps = nullptr;          // one bin's taps, laid out like its G block
     int64_t sur_taps_bytes = 0;
@@ -186,6 +186,7 @@ enum Stage { ST_FWD_ROWS = 0, ST_FWD_COLS = 1, ST_CLEAR = 2, ST_GTG = 3, ST_INV_
 
 constexpr int FX_HMAX = 5;      // max over entries of H of |h.x| + |h.y| (float bits)
 constexpr int FX_BX = 6;        // image bound B_x of the current Phi^dagger Phi apply (float)
+constexpr int FX_YB = 7;        // max |y.x| + |y.y| of the current Phi^dagger apply (float)
 
 // Fixed-point grid step.  The grid step accumulates each tile patch in two 32-bit integer
 // words per real number (hi: the contribution scaled by a power of two s and rounded;
@@ -197,7 +198,7 @@ constexpr int FX_BX = 6;        // image bound B_x of the current Phi^dagger Phi
 // d_fx layout (32-bit words):
 constexpr int FX_TMAX = 0;      // max over taps of |t.x| + |t.y| (float bits; plan time)
 constexpr int FX_T1 = 1;        // max over visibilities of sum over taps of |t.x| + |t.y|
-constexpr int FX_MAXTERM = 2;   // bound on |contribution| of the current apply (float)
+constexpr int FX_MAXTERM = 2;   // bound on |contribution| of a Phi^dagger Phi apply from the image (float)
 constexpr int FX_YMAX = 3;      // running max of |y.x| + |y.y| (float bits)
 constexpr int FX_COUNT = 4;     // blocks done (last-block reduction)
 constexpr int FX_PART = 64;     // per-block partial sums
@@ -221,6 +222,9 @@ void launch_inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, 
 void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,
                 cudaStream_t s);
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
+// exact tiles of the sorted visibilities [v0, v0 + n) into their block (the on-the-fly mode's
+// scratch), with the tap bounds of the fixed-point grid step
+void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t s);
 
 // The three applies on stream s (defined in apply.cu).
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s);

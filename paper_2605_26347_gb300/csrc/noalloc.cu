@@ -52,7 +52,7 @@ extern "C" rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t p, const rimo_
         if (!p) fail(RIMO_ERR_INVALID_ARG, "null plan");
         if (!x || !out) fail(RIMO_ERR_INVALID_ARG, "null buffer");
         if ((const void*)x == (const void*)out) fail(RIMO_ERR_INVALID_ARG, "x and out must be distinct");
-        if (p->mode == RIMO_MODE_SURROGATE || p->h_built)
+        if (p->mode != RIMO_MODE_STORED_G || p->h_built)
             fail(RIMO_ERR_UNSUPPORTED, "the allocation-free apply covers stored-G plans only");
         const size_t counters = align256((size_t)p->P * sizeof(int32_t));
         const size_t ab = align256((size_t)2 * p->nx * p->ny * sizeof(float2));

@@ -239,11 +239,13 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     fill_estimate(&p->info, ch, M, p->L);
     p->P = ch.P;
     p->mode = ch.mode;
-    if (p->mode == RIMO_MODE_ONTHEFLY) fail(RIMO_ERR_UNSUPPORTED, "exact on-the-fly kernels are not built");
     const bool surrogate = p->mode == RIMO_MODE_SURROGATE;
+    // tiles generated per bin at apply time, by the network or exactly (no stored G)
+    // (a holographic plan stores no G either: Phi and Phi^dagger, and Phi^dagger Phi until
+    // rimo_build_holographic has run, generate exact tiles on the fly; Fig. 2 regimes b, c)
+    const bool generated = surrogate || p->mode == RIMO_MODE_ONTHEFLY || p->mode == RIMO_MODE_HOLOGRAPHIC;
     if (surrogate && (q.kb_support + q.max_wsupport - 1 != 15))
         fail(RIMO_ERR_UNSUPPORTED, "the kernel surrogate generates 15 x 15 tiles: kb_support + max_wsupport - 1 must be 15");
-    if (p->mode == RIMO_MODE_HOLOGRAPHIC) p->holographic = false;  // G first, H on request
 
     // ---- w-bins on the subset, every visibility to its nearest bin (Section 3.1)
     std::vector<double> w_sub = planner::subset_w(uvw, M, q.seed, q.plan_fraction);
@@ -372,7 +374,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     double limit = q.block_bytes_max > 0 ? (double)q.block_bytes_max : 8.0 * 1073741824.0;
     if (q.n_blocks > 0) limit = std::ceil(total_bytes / q.n_blocks);
     limit = std::max(limit, std::ceil(total_bytes / 200.0));
-    if (surrogate) limit = 1e300;  // one block per bin: its taps are generated into one scratch
+    if (generated) limit = 1e300;  // one block per bin: its taps are generated into one scratch
     std::vector<VisMeta> meta(M);
     std::vector<float> wr_s(M), pu_s(M), pv_s(M);
     p->bins.assign(P, BinRange());
@@ -498,9 +500,9 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->d_phiv = upload(p, pv_s, s);
     int64_t gbytes = 0;
     std::vector<float2*> ptrs;
-    if (surrogate) {
-        // no stored G: every bin's (single) block points at one scratch that the surrogate
-        // refills for each bin of each apply
+    if (generated) {
+        // no stored G: every bin's (single) block points at one scratch that is refilled
+        // for each bin of each apply
         int64_t mx = 16;
         for (int64_t bb : p->block_bytes) mx = std::max(mx, bb);
         p->d_sur_taps = (float2*)dev_alloc(p, (size_t)mx);
@@ -572,7 +574,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     p->info.n_tiles = n_active;
 
     // ---- stage 3: precompute G on the device (the surrogate generates it at apply time)
-    if (!surrogate) {
+    if (!generated) {
         prof_begin(p, ST_GBUILD, s);
         launch_gbuild(p, s);
         prof_end(p, 1, s);
@@ -683,8 +685,8 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
     try {
         if (!p || (n > 0 && (!idx || !g0 || !h0 || !S || !taps)) || n < 0)
             fail(RIMO_ERR_INVALID_ARG, "null pointer or n < 0");
-        if (p->mode == RIMO_MODE_SURROGATE)
-            fail(RIMO_ERR_UNSUPPORTED, "a surrogate plan stores no tiles (they are generated per bin at apply time)");
+        if (p->mode != RIMO_MODE_STORED_G)
+            fail(RIMO_ERR_UNSUPPORTED, "this plan stores no tiles (they are generated per bin at apply time)");
         cudaStream_t s = (cudaStream_t)stream;
         for (int64_t q = 0; q < n; ++q) {
             if (idx[q] < 0 || idx[q] >= p->M) fail(RIMO_ERR_INVALID_ARG, "visibility index out of range");

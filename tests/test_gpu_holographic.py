@@ -92,3 +92,23 @@ def test_dense_coverage_parity():
     ref = op.phi_adj_phi(x.astype(np.complex128))
     assert rel(g_path, ref) < TOL
     assert rel(h_path, ref) < TOL
+
+
+def test_holographic_plan_without_stored_g():
+    # a plan in holographic mode keeps no G: tiles on the fly, then H built bin by bin
+    # from freshly generated exact tiles (Fig. 2, regime b)
+    import paper_2605_26347_gb300 as pkg
+    w = synth.make_config(1)
+    fov = w.fov_rad
+    plan, op = both(w.uvw, 256, 256, fov, fov, n_wbins=4, mode=pkg.MODE_HOLOGRAPHIC)
+    assert plan.info()["g_bytes"] < 0.05 * op.plan.K * 8
+    ref = op.phi_adj_phi(w.sky.astype(np.complex128))
+    assert rel(to_host(plan.phi_adj_phi(to_dev(w.sky))), ref) < TOL      # on the fly
+    assert rel(to_host(plan.phi(to_dev(w.sky))), op.phi(w.sky.astype(np.complex128))) < TOL
+    plan.build_holographic()
+    assert rel(to_host(plan.phi_adj_phi(to_dev(w.sky))), ref) < TOL      # through H
+    H = op.holographic(1).tocoo()
+    pick = np.random.default_rng(3).choice(H.nnz, size=200, replace=False)
+    r, c = H.row[pick], H.col[pick]
+    pairs = np.stack([r // op.gy, r % op.gy, c // op.gy, c % op.gy], axis=1)
+    assert rel(plan.holographic_entries(1, pairs), H.data[pick]) < TOL
