@@ -237,6 +237,16 @@ rimo_status rimo_build_holographic(rimo_plan_t plan, void* stream);
 rimo_status rimo_plan_get_holographic(rimo_plan_t plan, int32_t bin, const int32_t* pairs, int64_t n,
                                       rimo_cfloat* out, void* stream);
 
+/*
+ * out = sum over the w-bins p with bin_mask[p] != 0 of Phi_p^dagger Phi_p x (the terms of
+ * Eq. 7), for sharding the bins over devices or processes whose partial images are then
+ * summed.  bin_mask: host, P bytes (rimo_plan_info.P); NULL selects every bin.  No
+ * selected bin (or only empty ones) gives out = 0.  Layout, streams and errors as
+ * rimo_apply_phi_adj_phi.
+ */
+rimo_status rimo_apply_phi_adj_phi_bins(rimo_plan_t plan, const rimo_cfloat* x_dev, rimo_cfloat* out_dev,
+                                        int32_t real_part_only, const uint8_t* bin_mask, void* stream);
+
 /* PSF: out = Phi^dagger Phi delta, delta at pixel (ny/2, nx/2); unnormalised. */
 rimo_status rimo_psf(rimo_plan_t plan, rimo_cfloat* out_dev, void* stream);
 

@@ -174,11 +174,12 @@ class Operator:
             out += np.conj(self.z_layer(p)) * self.adj_grid(Xh)
         return out
 
-    def phi_adj_phi(self, x: np.ndarray, real_part_only: bool = False) -> np.ndarray:
+    def phi_adj_phi(self, x: np.ndarray, real_part_only: bool = False, bins=None) -> np.ndarray:
+        """sum_p Phi_p^dagger Phi_p x (Eq. 7), over all w-bins or the listed ones."""
         pp = self.pp
         x = np.asarray(x, dtype=np.complex128)
         out = np.zeros((pp.ny, pp.nx), dtype=np.complex128)
-        for p in range(self.plan.P):
+        for p in (range(self.plan.P) if bins is None else bins):
             if self.G[p].shape[0] == 0:
                 continue
             Zp = self.z_layer(p)

@@ -169,6 +169,19 @@ class Plan:
     def build_holographic(self, stream=None):
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 
+    def phi_adj_phi_bins(self, x, bin_mask, out=None, real_part_only=False, stream=None):
+        """sum over the w-bins with bin_mask[p] != 0 of Phi_p^dagger Phi_p x (rimo_apply_phi_adj_phi_bins)."""
+        torch = _torch()
+        _check_image(x, self.ny, self.nx, "x")
+        m = np.ascontiguousarray(np.asarray(bin_mask, dtype=np.uint8))
+        if m.size != self.info()["P"]:
+            raise ValueError("bin_mask needs one entry per w-bin")
+        if out is None:
+            out = torch.empty_like(x)
+        _lib.check(self._lib.rimo_apply_phi_adj_phi_bins(self._h, x.data_ptr(), out.data_ptr(), int(real_part_only),
+                                                         m.ctypes.data, _stream_ptr(stream)))
+        return out
+
     def set_surrogate(self, sur: "Surrogate") -> None:
         """rimo_plan_set_surrogate: generate this (surrogate-mode) plan's tiles with `sur`."""
         _lib.check(self._lib.rimo_plan_set_surrogate(self._h, sur._h))

@@ -87,6 +87,7 @@ _PROTOS = {
     "rimo_apply_phi_adj": (C.c_int, [_P, _P, _P, _P]),
     "rimo_apply_phi_adj_phi": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "rimo_apply_phi_adj_phi_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
+    "rimo_apply_phi_adj_phi_bins": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "rimo_build_holographic": (C.c_int, [_P, _P]),
     "rimo_plan_get_holographic": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, _P]),
     "rimo_psf": (C.c_int, [_P, _P, _P]),

@@ -132,13 +132,18 @@ void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s) {
 }
 
 void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s) {
+    apply_phi_adj_phi_bins(p, x, out, real_only, nullptr, s);
+}
+
+void apply_phi_adj_phi_bins(rimo_plan* p, const float2* x, float2* out, int real_only, const uint8_t* mask,
+                            cudaStream_t s) {
     bool first = true;
     begin_apply(p, s);
     prof_begin(p, ST_BOUND, s);
     launch_image_bound(p, x, s);
     prof_end(p, 1, s);
     for (int b = 0; b < p->P; ++b) {
-        if (bin_empty(p, b)) continue;
+        if (bin_empty(p, b) || (mask && !mask[b])) continue;
         fwd(p, b, x, s);
         if (p->h_built) {
             // H_p in place of G_p^dagger G_p (Section 3.3)
@@ -186,6 +191,17 @@ rimo_status rimo_apply_phi_adj_phi(rimo_plan_t p, const rimo_cfloat* x, rimo_cfl
     if (!x || !out) fail(RIMO_ERR_INVALID_ARG, "null buffer");
     if ((const void*)x == (const void*)out) fail(RIMO_ERR_INVALID_ARG, "x and out must be distinct");
     apply_phi_adj_phi(p, (const float2*)x, (float2*)out, real_part_only, (cudaStream_t)stream);
+    RIMO_CUDA(cudaGetLastError());
+    RIMO_API_END
+}
+
+rimo_status rimo_apply_phi_adj_phi_bins(rimo_plan_t p, const rimo_cfloat* x, rimo_cfloat* out,
+                                        int32_t real_part_only, const uint8_t* bin_mask, void* stream) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    if (!x || !out) fail(RIMO_ERR_INVALID_ARG, "null buffer");
+    if ((const void*)x == (const void*)out) fail(RIMO_ERR_INVALID_ARG, "x and out must be distinct");
+    apply_phi_adj_phi_bins(p, (const float2*)x, (float2*)out, real_part_only, bin_mask, (cudaStream_t)stream);
     RIMO_CUDA(cudaGetLastError());
     RIMO_API_END
 }

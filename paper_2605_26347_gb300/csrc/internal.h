@@ -230,6 +230,9 @@ void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s);
 void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s);
 void apply_phi_adj_phi(rimo_plan* p, const float2* x, float2* out, int real_only, cudaStream_t s);
+// the same over the bins with mask[b] != 0 (mask: host, P entries; NULL: all bins)
+void apply_phi_adj_phi_bins(rimo_plan* p, const float2* x, float2* out, int real_only, const uint8_t* mask,
+                            cudaStream_t s);
 // bound on the grid-step contributions of Phi^dagger Phi x (from the image x) or of
 // Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);

@@ -204,3 +204,38 @@ def test_large_image_parity(n):
     assert rel(to_host(plan.phi(to_dev(x))), op.phi(x.astype(np.complex128))) < TOL
     assert rel(to_host(plan.phi_adj(to_dev(y))), op.phi_adj(y.astype(np.complex128))) < TOL
     assert rel(to_host(plan.phi_adj_phi(to_dev(x))), op.phi_adj_phi(x.astype(np.complex128))) < TOL
+
+
+def test_bin_subsets_sum_to_the_full_apply(mono256):
+    # Eq. 7 term by term: disjoint bin subsets add up to Phi^dagger Phi
+    import torch
+    w, plan, op = mono256
+    xd = to_dev(w.sky)
+    P = plan.info()["P"]
+    m1 = np.zeros(P, np.uint8)
+    m1[::2] = 1
+    a = to_host(plan.phi_adj_phi_bins(xd, m1))
+    b = to_host(plan.phi_adj_phi_bins(xd, 1 - m1))
+    full = to_host(plan.phi_adj_phi(xd))
+    assert rel(a + b, full) < 1e-6
+    assert rel(a, op.phi_adj_phi(w.sky.astype(np.complex128), bins=list(np.nonzero(m1)[0]))) < TOL
+    assert not np.any(to_host(plan.phi_adj_phi_bins(xd, np.zeros(P, np.uint8))))
+    torch.cuda.synchronize()
+
+
+def test_sharded_apply_on_one_nccl_rank(mono256):
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_2605_26347_gb300 import distributed as rd
+    w, plan, _ = mono256
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        xd = to_dev(w.sky)
+        got = to_host(rd.sharded_phi_adj_phi(plan, xd))
+        assert rel(got, to_host(plan.phi_adj_phi(xd))) < 1e-6
+    finally:
+        dist.destroy_process_group()
