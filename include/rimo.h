@@ -185,7 +185,11 @@ rimo_status rimo_plan_get_bins(rimo_plan_t plan, double* w_stack, int32_t* bins,
  * g0[q], h0[q] (first grid cell along u and v, already reduced modulo the grid),
  * S[q] (tile side) and taps[q * 19 * 19 ...]: the S x S tile, row a along u, column b
  * along v, at taps + q * 361 (row stride S).  Synchronises `stream`.
- * Errors: INVALID_ARG, UNSUPPORTED (plan without stored G).
+ * Plans without stored G (surrogate, on-the-fly, holographic before H is built) generate
+ * the requested visibilities' bins into their tap scratch, as an apply does, and copy
+ * from there; such a call must not overlap an apply of the same plan.
+ * Errors: INVALID_ARG, STATE (surrogate plan without a surrogate), UNSUPPORTED
+ * (holographic plan whose tiles were folded into H), CUDA.
  */
 rimo_status rimo_plan_get_tiles(rimo_plan_t plan, const int64_t* idx, int64_t n, int32_t* g0,
                                 int32_t* h0, int32_t* S, rimo_cfloat* taps, void* stream);
@@ -398,8 +402,11 @@ rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_par
  * scratch the size of the largest bin, then grids them as the stored-G path does.
  * rimo_plan_set_surrogate attaches s (not owned; it must outlive its use, and one
  * surrogate must not serve two applies at once) and allocates the generation buffers.
- * Applies of a surrogate plan without a surrogate fail with STATE; rimo_plan_get_tiles,
+ * Applies and tile read-back of a surrogate plan without a surrogate fail with STATE;
  * rimo_build_holographic and the allocation-free apply return UNSUPPORTED.
+ * The generator runs the whole network per 128 visibilities in one persistent kernel
+ * (BF16 operands on the tensor cores, FP32 accumulation, layer 1 and GELU in FP32,
+ * hidden activations rounded to BF16 as in rimo_surrogate_forward).
  * Errors: INVALID_ARG (plan not in surrogate mode, other device), OOM, CUDA.
  */
 rimo_status rimo_plan_set_surrogate(rimo_plan_t plan, rimo_surrogate_t s);

@@ -471,8 +471,8 @@ void Mlp::step(const float* X, const float* T, int B, float lr, cudaStream_t s) 
 // C ABI
 struct rimo_surrogate {
     rimo::Mlp mlp;
-    float w_scale = 0.f;        // input normalisation of w_r (set by rimo_surrogate_fit)
-    float* Xin = nullptr;       // generation inputs [SUR_SUB][3]
+    float w_scale = 0.f;          // input normalisation of w_r (set by rimo_surrogate_fit)
+    __nv_bfloat16* W3g = nullptr;  // layer 3 for the tile generator: [480][128], see sur_gen_kernel
 };
 
 namespace rimo {
@@ -518,7 +518,6 @@ using namespace rimo;
 
 namespace rimo {
 
-constexpr int SUR_SUB = 1 << 16;  // visibilities per generation sub-batch (a multiple of 128)
 constexpr int SUR_S = 15;         // tile side the network outputs
 constexpr int SUR_TAPS = SUR_S * SUR_S;
 
@@ -530,66 +529,251 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-// network inputs (2 phi_u - 1, 2 phi_v - 1, w_r / w_scale) of sorted visibilities
-// [v0, v0 + n); rows n .. B-1 repeat the last visibility (their outputs are not used)
-__global__ void sur_inputs_kernel(const float* __restrict__ phiu, const float* __restrict__ phiv,
-                                  const float* __restrict__ wr, int64_t v0, int n, int B, float inv_w, float* X) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B) return;
-    const int64_t k = v0 + (j < n ? j : n - 1);
-    X[3 * j + 0] = 2.f * phiu[k] - 1.f;
-    X[3 * j + 1] = 2.f * phiv[k] - 1.f;
-    X[3 * j + 2] = wr[k] * inv_w;
+// ---- tile generator: the whole network per 128 visibilities in one persistent CTA per SM
+// Layer 1 (3 -> 128) on CUDA cores into shared memory (bf16, canonical K-major); layer 2 as
+// 8 MMAs (M 128, N 128, K 16) into TMEM columns [0, 128); GELU read-out back into the same
+// shared buffer; layer 3 as 2 x 8 MMAs (N 256 + 224) into TMEM columns [0, 480); the read-out
+// adds b3 and writes each visibility's 15 x 15 complex tile (plus its even-count pad) to
+// the tap scratch at the visibility's offset.  W2 and W3 stay in shared memory (bf16).
+// Layer 3's rows are packed so that real and imaginary outputs start at 16-aligned TMEM
+// columns: rows [0, 225) the real parts, [240, 465) the imaginary parts, the rest zero.
+constexpr int GEN_THREADS = 256;
+constexpr int GEN_N3 = 480, GEN_IM = 240;
+constexpr size_t GEN_SW2 = (size_t)MLP_H * MLP_H * 2, GEN_SW3 = (size_t)GEN_N3 * MLP_H * 2, GEN_SA = 128 * MLP_H * 2;
+constexpr size_t GEN_SMEM = GEN_SW2 + GEN_SW3 + GEN_SA + (384 + 128 + 128 + GEN_N3 + 384) * 4 + 128 * 8;
+
+__global__ void pack_w3g_kernel(const float* __restrict__ P, bf16* __restrict__ W3g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= GEN_N3 * MLP_H) return;
+    const int r = i / MLP_H, c = i % MLP_H;
+    int src = -1;
+    if (r < SUR_TAPS) src = r;
+    else if (r >= GEN_IM && r < GEN_IM + SUR_TAPS) src = SUR_TAPS + (r - GEN_IM);
+    W3g[i] = __float2bfloat16(src >= 0 ? P[MLP_OFF_W3 + src * MLP_H + c] : 0.f);
 }
 
-// one warp per visibility: tile q = (Y[q] + b3[q], Y[225 + q] + b3[225 + q]) into the tap
-// scratch at the visibility's offset, plus the tap bounds of the fixed-point grid step
-__global__ void sur_outputs_kernel(const float* __restrict__ Y, const float* __restrict__ b3,
-                                   const VisMeta* __restrict__ meta, int64_t v0, int n, float2* __restrict__ taps,
-                                   uint32_t* fx) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const float* y = Y + (size_t)warp * MLP_OUT_PAD;
-    float2* t = taps + meta[v0 + warp].off;
-    float tmax = 0.f, tsum = 0.f;
-    for (int q = lane; q < SUR_TAPS + 1; q += 32) {  // 225 taps and the even-count pad
-        float2 v = make_float2(0.f, 0.f);
-        if (q < SUR_TAPS) v = make_float2(y[q] + b3[q], y[SUR_TAPS + q] + b3[SUR_TAPS + q]);
-        t[q] = v;
-        const float m = fabsf(v.x) + fabsf(v.y);
-        tmax = fmaxf(tmax, m);
-        tsum += m;
+struct GenArgs {
+    const VisMeta* meta;
+    float2* taps;
+    const float* phiu;
+    const float* phiv;
+    const float* wr;
+    int64_t v0;
+    int n;
+    float inv_w;
+    const float* P;    // FP32 parameters (W1, b1, b2, b3)
+    const bf16* W2b;   // [128][128]
+    const bf16* W3g;   // [480][128]
+    uint32_t* fx;
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* sW2 = sm;
+    unsigned char* sW3 = sm + GEN_SW2;
+    unsigned char* sA = sW3 + GEN_SW3;
+    float* sW1 = reinterpret_cast<float*>(sA + GEN_SA);
+    float* sb1 = sW1 + 384;
+    float* sb2 = sb1 + 128;
+    float* sb3 = sb2 + 128;
+    float* sx = sb3 + GEN_N3;
+    int64_t* soff = reinterpret_cast<int64_t*>(sx + 384);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < MLP_H * 16; e += GEN_THREADS) {
+        const int r = e >> 4, v = e & 15;
+        *reinterpret_cast<uint4*>(sW2 + tc::kmajor_offset(r, v * 8, MLP_H)) =
+            *reinterpret_cast<const uint4*>(A.W2b + (size_t)r * MLP_H + v * 8);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    for (int e = tid; e < GEN_N3 * 16; e += GEN_THREADS) {
+        const int r = e >> 4, v = e & 15;
+        *reinterpret_cast<uint4*>(sW3 + tc::kmajor_offset(r, v * 8, GEN_N3)) =
+            *reinterpret_cast<const uint4*>(A.W3g + (size_t)r * MLP_H + v * 8);
     }
-    if (lane == 0) {
-        atomicMax(fx + FX_TMAX, __float_as_uint(tmax));
-        atomicMax(fx + FX_T1, __float_as_uint(tsum));
+    for (int e = tid; e < 384; e += GEN_THREADS) sW1[e] = __bfloat162float(__float2bfloat16(A.P[MLP_OFF_W1 + e]));
+    for (int e = tid; e < 128; e += GEN_THREADS) {
+        sb1[e] = A.P[MLP_OFF_B1 + e];
+        sb2[e] = A.P[MLP_OFF_B2 + e];
+    }
+    for (int e = tid; e < GEN_N3; e += GEN_THREADS) {
+        int src = -1;
+        if (e < SUR_TAPS) src = e;
+        else if (e >= GEN_IM && e < GEN_IM + SUR_TAPS) src = SUR_TAPS + (e - GEN_IM);
+        sb3[e] = src >= 0 ? A.P[MLP_OFF_B3 + src] : 0.f;
+    }
+    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        mbar_init_(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+    uint32_t phase = 0;
+    bool ok = true;
+    const int ntile = (A.n + 127) / 128;
+    for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
+        const int base = tile * 128;
+        if (tid < 128) {
+            const int j = base + tid < A.n ? base + tid : A.n - 1;
+            const int64_t k = A.v0 + j;
+            sx[3 * tid + 0] = 2.f * A.phiu[k] - 1.f;
+            sx[3 * tid + 1] = 2.f * A.phiv[k] - 1.f;
+            sx[3 * tid + 2] = A.wr[k] * A.inv_w;
+            soff[tid] = A.meta[k].off;
+        }
+        __syncthreads();
+        {   // layer 1: row r, hidden units [64 h, 64 h + 64)
+            const int r = tid & 127, h = tid >> 7;
+            const float x0 = sx[3 * r], x1 = sx[3 * r + 1], x2 = sx[3 * r + 2];
+#pragma unroll 1
+            for (int g = 0; g < 8; ++g) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float z[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = 64 * h + 8 * g + 2 * q + u;
+                        z[u] = gelu_f(fmaf(x0, sW1[3 * j], fmaf(x1, sW1[3 * j + 1], fmaf(x2, sW1[3 * j + 2], sb1[j]))));
+                    }
+                    w[q] = pack_bf2(z[0], z[1]);
+                }
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, 64 * h + 8 * g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {  // layer 2
+            for (int s = 0; s < MLP_H / 16; ++s)
+                tc::mma_bf16(tmem, tc::smem_desc(tc::smem_addr(sA) + s * 128 * 32, 128, 256),
+                             tc::smem_desc(tc::smem_addr(sW2) + s * MLP_H * 32, 128, 256), tc::idesc_bf16_f32(128, 128),
+                             s > 0 ? 1u : 0u);
+            tc::mma_commit(&bar);
+        }
+        ok = mbar_wait_(&bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        tc::fence_after_sync();
+        {   // layer-2 read-out: row 32 (warp % 4) + lane, columns [64 (warp / 4), + 64)
+            const int r = 32 * (warp & 3) + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                const int col = 64 * (warp >> 2) + c0;
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)col, v);
+                uint32_t w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    w[i] = pack_bf2(gelu_f(v[2 * i] + sb2[col + 2 * i]), gelu_f(v[2 * i + 1] + sb2[col + 2 * i + 1]));
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, col, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, col + 8, 128)) = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {  // layer 3: rows [0, 256) and [256, 480) of W3g
+            for (int s = 0; s < MLP_H / 16; ++s) {
+                const uint64_t ad = tc::smem_desc(tc::smem_addr(sA) + s * 128 * 32, 128, 256);
+                const uint32_t b0 = tc::smem_addr(sW3) + s * GEN_N3 * 32;
+                tc::mma_bf16(tmem, ad, tc::smem_desc(b0, 128, 256), tc::idesc_bf16_f32(128, 256), s > 0 ? 1u : 0u);
+                tc::mma_bf16(tmem + 256, ad, tc::smem_desc(b0 + (256 / 8) * 256, 128, 256),
+                             tc::idesc_bf16_f32(128, GEN_N3 - 256), s > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&bar);
+        }
+        ok = mbar_wait_(&bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        tc::fence_after_sync();
+        {   // layer-3 read-out: chunks of 16 taps; warps 0-3 the even chunks, 4-7 the odd ones
+            const int r = 32 * (warp & 3) + lane;
+            const bool valid = base + r < A.n;
+            float2* dst = A.taps + soff[r];
+            float tmax = 0.f, tsum = 0.f;
+#pragma unroll 1
+            for (int c = warp >> 2; c < (SUR_TAPS + 15) / 16; c += 2) {
+                const int q0 = 16 * c;
+                float re[16], im[16];
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)q0, re);
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)(GEN_IM + q0), im);
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const int q = q0 + i;
+                    if (q > SUR_TAPS) break;  // q = 224, 225: the last tap and the pad
+                    float2 t0 = make_float2(re[i] + sb3[q], im[i] + sb3[GEN_IM + q]);
+                    float2 t1 = q + 1 < SUR_TAPS ? make_float2(re[i + 1] + sb3[q + 1], im[i + 1] + sb3[GEN_IM + q + 1])
+                                                 : make_float2(0.f, 0.f);
+                    const float m0 = fabsf(t0.x) + fabsf(t0.y), m1 = fabsf(t1.x) + fabsf(t1.y);
+                    tmax = fmaxf(tmax, fmaxf(m0, m1));
+                    tsum += m0 + m1;
+                    if (valid) *reinterpret_cast<float4*>(dst + q) = make_float4(t0.x, t0.y, t1.x, t1.y);
+                }
+            }
+            if (valid) {
+                // each warp group sees half the taps of a row: the row's tap sum is at most
+                // twice the larger half
+                atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
+                atomicMax(A.fx + FX_T1, __float_as_uint(2.f * tsum));
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok && tid == 0) atomicExch(A.status, 2);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) {
+        tc::tmem_dealloc(tmem, 512);
+        tc::tmem_relinquish();
     }
 }
 
 void reset_surrogate_bounds(rimo_plan* p, cudaStream_t s) {
     RIMO_CUDA(cudaMemsetAsync(p->d_fx + FX_TMAX, 0, 2 * sizeof(uint32_t), s));  // FX_TMAX, FX_T1
+    if (p->mode == RIMO_MODE_SURROGATE)  // this apply's network (it may have trained since)
+        pack_w3g_kernel<<<(GEN_N3 * MLP_H + 255) / 256, 256, 0, s>>>(p->sur->mlp.P, p->sur->W3g);
 }
 
 int surrogate_generate(rimo_plan* p, int bin, cudaStream_t s) {
     rimo_surrogate* sur = p->sur;
-    Mlp& m = sur->mlp;
     const float ws = sur->w_scale > 0.f ? sur->w_scale : (p->info.wr_max > 0 ? (float)p->info.wr_max : 1.f);
-    const int64_t vb = p->bins[bin].vb, ve = p->bins[bin].ve;
-    int launches = 0;
-    for (int64_t v0 = vb; v0 < ve; v0 += SUR_SUB) {
-        const int n = (int)std::min<int64_t>(SUR_SUB, ve - v0);
-        const int B = (n + 127) / 128 * 128;
-        sur_inputs_kernel<<<(B + 255) / 256, 256, 0, s>>>(p->d_phiu, p->d_phiv, p->d_wr, v0, n, B, 1.f / ws, sur->Xin);
-        m.forward(sur->Xin, B, s);
-        sur_outputs_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(m.Y, m.P + MLP_OFF_B3, p->d_meta, v0, n,
-                                                                 p->d_sur_taps, p->d_fx);
-        launches += 6;
-    }
-    return launches;
+    const int64_t vb = p->bins[bin].vb, n = p->bins[bin].ve - vb;
+    if (n <= 0) return 0;
+    GenArgs A;
+    A.meta = p->d_meta;
+    A.taps = p->d_sur_taps;
+    A.phiu = p->d_phiu;
+    A.phiv = p->d_phiv;
+    A.wr = p->d_wr;
+    A.v0 = vb;
+    A.n = (int)n;
+    A.inv_w = 1.f / ws;
+    A.P = sur->mlp.P;
+    A.W2b = sur->mlp.W2b;
+    A.W3g = sur->W3g;
+    A.fx = p->d_fx;
+    A.status = p->d_status;
+    RIMO_CUDA(cudaFuncSetAttribute(sur_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEN_SMEM));
+    const int64_t ntile = (n + 127) / 128;
+    const int grid = (int)std::min<int64_t>(ntile, (int64_t)p->n_sm);
+    sur_gen_kernel<<<grid, GEN_THREADS, GEN_SMEM, s>>>(A);
+    return 1;
 }
 
 // training sample i: a visibility k drawn uniformly, its inputs, and its exact tile embedded
@@ -740,8 +924,7 @@ rimo_status rimo_plan_set_surrogate(rimo_plan_t p, rimo_surrogate_t s) {
     RIMO_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) fail(RIMO_ERR_INVALID_ARG, "plan and surrogate on different devices");
     // everything the generation needs is allocated here, not during an apply
-    s->mlp.reserve(SUR_SUB);
-    if (!s->Xin) s->Xin = (float*)s->mlp.alloc((size_t)SUR_SUB * 3 * sizeof(float));
+    if (!s->W3g) s->W3g = (bf16*)s->mlp.alloc((size_t)GEN_N3 * MLP_H * sizeof(bf16));
     p->sur = s;
     SUR_END
 }

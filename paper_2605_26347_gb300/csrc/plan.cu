@@ -685,11 +685,22 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
     try {
         if (!p || (n > 0 && (!idx || !g0 || !h0 || !S || !taps)) || n < 0)
             fail(RIMO_ERR_INVALID_ARG, "null pointer or n < 0");
-        if (p->mode != RIMO_MODE_STORED_G)
-            fail(RIMO_ERR_UNSUPPORTED, "this plan stores no tiles (they are generated per bin at apply time)");
+        const bool generated = p->mode != RIMO_MODE_STORED_G;
+        if (p->mode == RIMO_MODE_SURROGATE && !p->sur)
+            fail(RIMO_ERR_STATE, "surrogate plan without a surrogate (rimo_plan_set_surrogate)");
+        if (p->mode == RIMO_MODE_HOLOGRAPHIC && p->h_built)
+            fail(RIMO_ERR_UNSUPPORTED, "holographic plan: its tiles were folded into H");
         cudaStream_t s = (cudaStream_t)stream;
-        for (int64_t q = 0; q < n; ++q) {
+        if (generated) reset_surrogate_bounds(p, s);
+        int have_bin = -1;  // the bin whose tiles the tap scratch holds
+        for (int64_t q = 0; q < n; ++q)
             if (idx[q] < 0 || idx[q] >= p->M) fail(RIMO_ERR_INVALID_ARG, "visibility index out of range");
+        std::vector<int64_t> order(n);  // requests grouped by bin: one generation per bin
+        for (int64_t q = 0; q < n; ++q) order[q] = q;
+        if (generated)
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int64_t a, int64_t b) { return p->bins_user[idx[a]] < p->bins_user[idx[b]]; });
+        for (int64_t q : order) {
             int64_t i = p->inv_perm[idx[q]];
             VisMeta m;
             RIMO_CUDA(cudaMemcpyAsync(&m, p->d_meta + i, sizeof(m), cudaMemcpyDeviceToHost, s));
@@ -697,6 +708,12 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
             int du = m.pos & 255, dv = (m.pos >> 8) & 255, Sq = (m.pos >> 16) & 255, blk = m.pos >> 24;
             // the tile containing sorted position i
             int b = p->bins_user[idx[q]];
+            if (generated && b != have_bin) {  // tiles of generated plans: this bin, as an apply makes them
+                RIMO_CUDA(cudaStreamSynchronize(s));  // earlier copies out of the scratch are done
+                if (p->mode == RIMO_MODE_SURROGATE) surrogate_generate(p, b, s);
+                else launch_gbuild_range(p, p->bins[b].vb, p->bins[b].ve - p->bins[b].vb, s);
+                have_bin = b;
+            }
             int tu = -1, tv = -1;
             for (int t = p->bins[b].t0; t < p->bins[b].t1; ++t)
                 if (p->tiles_host[t].vb <= i && i < p->tiles_host[t].ve) {  // the unit holding i
@@ -706,7 +723,9 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
             g0[q] = tu * p->TS + du;
             h0[q] = tv * p->TS + dv;
             S[q] = Sq;
-            RIMO_CUDA(cudaMemcpyAsync(taps + q * 361, p->d_gblocks[blk] + m.off,
+            // generated plans: every block is the one tap scratch
+            const float2* src = generated ? p->d_sur_taps : p->d_gblocks.at((size_t)blk);
+            RIMO_CUDA(cudaMemcpyAsync(taps + q * 361, src + m.off,
                                       (size_t)Sq * Sq * sizeof(float2), cudaMemcpyDeviceToHost, s));
         }
         RIMO_CUDA(cudaStreamSynchronize(s));

@@ -64,11 +64,39 @@ def test_surrogate_plan_stores_no_g(trained):
     w, exact, _, splan, _ = trained
     gi, si = exact.info(), splan.info()
     assert si["g_bytes"] < 0.01 * gi["g_bytes"]
-    with pytest.raises(pkg.RimoError) as e:
-        splan.tiles([0])
-    assert e.value.status == 6
     with pytest.raises(pkg.RimoError):
         splan.build_holographic()
+
+
+def test_generated_tiles_are_the_network_outputs(trained):
+    """The fused generator (one kernel per bin) against the batched network forward.
+
+    Inputs are rebuilt here from their definition: the fractional offsets of the first tap
+    on the oversampled grid and w_r = w - w_stack of the visibility's bin, scaled by w_scale.
+    """
+    w, _, sur, splan, _ = trained
+    fov = w.fov_rad
+    M = w.uvw.shape[0]
+    idx = np.sort(np.random.default_rng(3).choice(M, 640, replace=False))
+    g0, h0, S, tiles = splan.tiles(idx)
+    assert np.all(S == 15)
+    ws, bins, _ = splan.bins()
+    J = 7
+    tu = w.uvw[idx, 0] * (2.0 * fov) - J / 2.0
+    tv = w.uvw[idx, 1] * (2.0 * fov) - J / 2.0
+    pu = (tu - np.floor(tu)).astype(np.float32)
+    pv = (tv - np.floor(tv)).astype(np.float32)
+    wr = (w.uvw[idx, 2] - ws[bins[idx]]).astype(np.float32)
+    X = np.stack([2 * pu - 1, 2 * pv - 1, wr * np.float32(1.0 / sur.w_scale)], axis=1).astype(np.float32)
+    y = to_host(sur.forward(X)).astype(np.float64)
+    want = (y[:, :225] + 1j * y[:, 225:]).reshape(-1, 15, 15)
+    got = np.stack(tiles).astype(np.complex128)
+    assert rel(got, want) < 1e-4
+    assert np.max(np.abs(got - want)) < 1e-3 * np.max(np.abs(want))
+    # first cells: floor of the continuous position plus one, less the w-kernel half-width
+    gx = 2 * 256
+    assert np.array_equal(g0, ((np.floor(tu).astype(np.int64) + 1 - 4) % gx).astype(np.int32))
+    assert np.array_equal(h0, ((np.floor(tv).astype(np.int64) + 1 - 4) % gx).astype(np.int32))
 
 
 def test_surrogate_plan_needs_a_network():
