@@ -547,9 +547,15 @@ void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Build of G (stage 3 of Fig. 3): one warp per visibility.
-//   1. residual w-kernel (Section 3.1, Fig. 1): tapered chirp c[a][b] on the L x L grid
-//      over twice the field of view, K(t) = (1/L^2) sum c e^{+2 pi i (t_x a_c + t_y b_c)/L}
-//      for the S_w x S_w central taps (row pass over a, then column pass over b);
+//   1. residual w-kernel (Section 3.1, Fig. 1): K(t) = (1/L^2) sum c[a][b] e^{+2 pi i
+//      (t_x a_c + t_y b_c)/L} over the L x L grid (a_c, b_c in [-L/2, L/2)) of the tapered
+//      chirp c.  c depends on lam and mu only through lam^2, mu^2, |lam| and |mu|, so it is
+//      even in a_c and in b_c (the edge a_c = -L/2 has no partner).  Summing each pair of
+//      signs first gives K(t) = (1/L^2) sum over a', b' in [0, L/2] of c(a', b') w(a', t_x)
+//      w(b', t_y) with real weights w(0, t) = 1, w(a', t) = 2 cos(2 pi a' t / L) and
+//      w(L/2, t) = cos(pi t): (L/2 + 1)^2 chirp samples instead of L^2, and K even in t_x
+//      and t_y, so only t in [0, h]^2 is summed.  Chirp samples go to shared memory, then
+//      a row pass over a' and a column pass over b';
 //   2. Kaiser-Bessel taps w_u[i] = KB(phi_u + J/2 - 1 - i), KB by Horner in
 //      rho = 1 - (2t/J)^2 of its normalised power series;
 //   3. T = w_u (*) K (*) w_v  (separable two-step convolution), S = S_w + J - 1.
@@ -559,10 +565,10 @@ struct BuildArgs {
     const float* phiu;
     const float* phiv;
     float2* const* gblk;
-    const float* wk_dn;
-    const float* tau_x;
+    const float* wk_dn;  // folded dn, Q x Q (Q = L/2 + 1)
+    const float* tau_x;  // folded tapers, Q
     const float* tau_y;
-    const float2* E;
+    const float* wc;     // folded weights w(a', t), Q x 8 (t < 5 used)
     const float* kb_coef;
     int kb_nterm;
     int L, hmax, J, literal;
@@ -579,95 +585,178 @@ __device__ __forceinline__ float kb_eval(float t, float invhalf, const float* co
     return acc;
 }
 
+constexpr int BUILD_TQ = 5;     // folded tap offsets t in [0, hmax], hmax <= 4
+constexpr int BUILD_WS = 8;     // row stride of the weight table (32 bytes: aligned float4 reads)
 constexpr int BUILD_WARPS = 8;
 
+// Chirp sample c(a', b') of the folded grid (a', b' in [0, L/2]) for residual w
+__device__ __forceinline__ float2 chirp_at(const float* s_dn, const float* s_tx, const float* s_ty, int Q,
+                                          int a, int b, float w, int literal) {
+    float sn, cs;
+    sincospif(2.f * w * s_dn[a * Q + b], &sn, &cs);
+    const float tt = s_tx[a] * s_ty[b];
+    return literal ? make_float2(tt * cs, -tt * sn) : make_float2(1.f + tt * (cs - 1.f), -tt * sn);
+}
+
+// L: the w-kernel grid side (16, 32, 64 or 128).  Row pass: the L/2 columns b' < L/2 are
+// spread over the lanes (F lanes per column when L/2 < 32, each summing a slice of a';
+// CPL columns per lane when L/2 > 32), with the chirp evaluated in registers; the edge
+// row a' = L/2 is added by every lane for its columns; the edge column b' = L/2 is a
+// warp reduction (a' over the lanes) plus the corner.
+template <int L>
 __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
-    extern __shared__ float smb[];
-    const int L = A.L, ns = 2 * A.hmax + 1;
-    float* s_dn = smb;                                // L * L
-    float* s_tx = s_dn + L * L;                       // L
-    float* s_ty = s_tx + L;                           // L
-    float* s_coef = s_ty + L;                         // 96
-    float2* s_E = reinterpret_cast<float2*>(s_coef + 96);  // L * ns
-    float2* s_w = s_E + L * ns;                       // per warp scratch
-    const int per_warp = L * 9 + 81 + 9 * 19 + 16;    // R, K, A, taps (float2 units)
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) s_dn[e] = A.wk_dn[e];
-    for (int e = threadIdx.x; e < L; e += blockDim.x) {
+    constexpr int NC = L / 2, Q = NC + 1;
+    constexpr int LW = NC < 32 ? NC : 32;        // lanes per a'-slice
+    constexpr int F = 32 / LW;                   // a'-slices (lanes per column)
+    constexpr int CPL = NC < 32 ? 1 : NC / 32;   // columns per lane
+    constexpr int APL = NC / F;                  // a' per slice
+    constexpr int EPL = (NC + 31) / 32;          // edge-column samples per lane
+    extern __shared__ __align__(16) float smb[];
+    float* s_wc = smb;                 // Q * BUILD_WS (first: 16-byte aligned rows)
+    float* s_dn = s_wc + Q * BUILD_WS; // Q * Q
+    float* s_tx = s_dn + Q * Q;        // Q
+    float* s_ty = s_tx + Q;            // Q
+    float* s_coef = s_ty + Q;          // 96
+    constexpr int TABF = (Q * BUILD_WS + Q * Q + 2 * Q + 96 + 1) & ~1;
+    constexpr int PER_WARP = Q * BUILD_TQ + BUILD_TQ * BUILD_TQ + 9 * 19 + 16;  // float2
+    float2* s_w = reinterpret_cast<float2*>(smb + TABF);
+    for (int e = threadIdx.x; e < Q * Q; e += blockDim.x) s_dn[e] = A.wk_dn[e];
+    for (int e = threadIdx.x; e < Q; e += blockDim.x) {
         s_tx[e] = A.tau_x[e];
         s_ty[e] = A.tau_y[e];
     }
     for (int e = threadIdx.x; e < A.kb_nterm; e += blockDim.x) s_coef[e] = A.kb_coef[e];
-    for (int e = threadIdx.x; e < L * ns; e += blockDim.x) s_E[e] = A.E[e];
+    for (int e = threadIdx.x; e < Q * BUILD_WS; e += blockDim.x) s_wc[e] = A.wc[e];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2* R = s_w + warp * per_warp;   // [b][s]  L x 9
-    float2* Kw = R + L * 9;              // [su][sv] 9 x 9
-    float2* Ab = Kw + 81;                // [su][b]  9 x 19
+    float2* R = s_w + warp * PER_WARP;      // [b'][t_x] Q x 5
+    float2* Kq = R + Q * BUILD_TQ;          // [t_x][t_y] 5 x 5
+    float2* Ab = Kq + BUILD_TQ * BUILD_TQ;  // [su][b]  9 x 19
     float* taps = reinterpret_cast<float*>(Ab + 9 * 19);  // wu[0..15], wv[16..31]
     const float invL2 = 1.f / ((float)L * (float)L);
     const float invhalf = 2.f / (float)A.J;
+    const int col0 = lane % LW, a_begin = (lane / LW) * APL;
     float tmax = 0.f;
     for (int64_t k = A.v0 + (int64_t)blockIdx.x * BUILD_WARPS + warp; k < A.v0 + A.nvis;
          k += (int64_t)gridDim.x * BUILD_WARPS) {
         float tsum = 0.f;
         const VisMeta mt = A.meta[k];
         const int S = (mt.pos >> 16) & 255;
-        const int Sw = S - A.J + 1, h = Sw >> 1, t0 = A.hmax - h;
+        const int Sw = S - A.J + 1, h = Sw >> 1, hq = h + 1;
         const float w = A.wr[k];
-        // 1a. row pass: R[b][s] = sum_a c[a][b] E[a][s + t0]
-        for (int b = lane; b < L; b += 32) {
-            float2 acc[9];
+        // 1a. row pass over a' < L/2 for this lane's columns, chirp in registers
+        float2 acc[CPL][BUILD_TQ];
 #pragma unroll
-            for (int s = 0; s < 9; ++s) acc[s] = make_float2(0.f, 0.f);
-            const float tb = s_ty[b];
-            for (int a = 0; a < L; ++a) {
-                float sn, cs;
-                sincospif(2.f * w * s_dn[a * L + b], &sn, &cs);
-                const float tt = s_tx[a] * tb;
-                float2 c;
-                if (A.literal) c = make_float2(tt * cs, -tt * sn);
-                else c = make_float2(1.f + tt * (cs - 1.f), -tt * sn);
-                const float2* Ea = s_E + a * ns + t0;
+        for (int j = 0; j < CPL; ++j)
 #pragma unroll
-                for (int s = 0; s < 9; ++s) {
-                    if (s < Sw) {
-                        const float2 e = Ea[s];
-                        acc[s].x = fmaf(c.x, e.x, fmaf(-c.y, e.y, acc[s].x));
-                        acc[s].y = fmaf(c.x, e.y, fmaf(c.y, e.x, acc[s].y));
+            for (int t = 0; t < BUILD_TQ; ++t) acc[j][t] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int a = a_begin; a < a_begin + APL; ++a) {
+            const float4 w03 = *reinterpret_cast<const float4*>(s_wc + a * BUILD_WS);
+            const float w4 = s_wc[a * BUILD_WS + 4];
+            const float wt[BUILD_TQ] = {w03.x, w03.y, w03.z, w03.w, w4};
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const float2 c = chirp_at(s_dn, s_tx, s_ty, Q, a, col0 + 32 * j, w, A.literal);
+#pragma unroll
+                for (int t = 0; t < BUILD_TQ; ++t) {
+                    acc[j][t].x = fmaf(wt[t], c.x, acc[j][t].x);
+                    acc[j][t].y = fmaf(wt[t], c.y, acc[j][t].y);
+                }
+            }
+        }
+        // the F slices of a column meet in every one of their lanes
+#pragma unroll
+        for (int o = LW; o < 32; o <<= 1)
+#pragma unroll
+            for (int j = 0; j < CPL; ++j)
+#pragma unroll
+                for (int t = 0; t < BUILD_TQ; ++t) {
+                    acc[j][t].x += __shfl_xor_sync(0xffffffffu, acc[j][t].x, o);
+                    acc[j][t].y += __shfl_xor_sync(0xffffffffu, acc[j][t].y, o);
+                }
+        // edge row a' = L/2 (weight (-1)^t), then the columns to shared memory
+        if (lane < LW) {
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int b = col0 + 32 * j;
+                const float2 c = chirp_at(s_dn, s_tx, s_ty, Q, NC, b, w, A.literal);
+#pragma unroll
+                for (int t = 0; t < BUILD_TQ; ++t) {
+                    const float sg = (t & 1) ? -1.f : 1.f;
+                    R[b * BUILD_TQ + t] = make_float2(fmaf(sg, c.x, acc[j][t].x), fmaf(sg, c.y, acc[j][t].y));
+                }
+            }
+        }
+        // edge column b' = L/2: sum over a' < L/2 across the lanes, plus the corner
+        {
+            float2 e[BUILD_TQ];
+#pragma unroll
+            for (int t = 0; t < BUILD_TQ; ++t) e[t] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < EPL; ++i) {
+                const int a = lane + 32 * i;
+                if (a < NC) {
+                    const float2 c = chirp_at(s_dn, s_tx, s_ty, Q, a, NC, w, A.literal);
+#pragma unroll
+                    for (int t = 0; t < BUILD_TQ; ++t) {
+                        const float wt = s_wc[a * BUILD_WS + t];
+                        e[t].x = fmaf(wt, c.x, e[t].x);
+                        e[t].y = fmaf(wt, c.y, e[t].y);
                     }
                 }
             }
+            if (lane == 0) {
+                const float2 c = chirp_at(s_dn, s_tx, s_ty, Q, NC, NC, w, A.literal);
 #pragma unroll
-            for (int s = 0; s < 9; ++s)
-                if (s < Sw) R[b * 9 + s] = acc[s];
+                for (int t = 0; t < BUILD_TQ; ++t) {
+                    const float sg = (t & 1) ? -1.f : 1.f;
+                    e[t].x = fmaf(sg, c.x, e[t].x);
+                    e[t].y = fmaf(sg, c.y, e[t].y);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < BUILD_TQ; ++t) {
+                    e[t].x += __shfl_xor_sync(0xffffffffu, e[t].x, o);
+                    e[t].y += __shfl_xor_sync(0xffffffffu, e[t].y, o);
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int t = 0; t < BUILD_TQ; ++t) R[NC * BUILD_TQ + t] = e[t];
         }
         // 2. KB taps
         if (lane < A.J) taps[lane] = kb_eval(A.phiu[k] + 0.5f * A.J - 1.f - lane, invhalf, s_coef, A.kb_nterm);
         else if (lane >= 16 && lane < 16 + A.J)
             taps[lane] = kb_eval(A.phiv[k] + 0.5f * A.J - 1.f - (lane - 16), invhalf, s_coef, A.kb_nterm);
         __syncwarp();
-        // 1b. column pass: K[su][sv] = (1/L^2) sum_b R[b][su] E[b][sv + t0]
-        for (int e = lane; e < Sw * Sw; e += 32) {
-            const int su = e / Sw, sv = e - su * Sw;
+        // 1b. column pass: K(t_x, t_y) = (1/L^2) sum_b' R[b'][t_x] w(b', t_y)
+        if (lane < hq * hq) {
+            const int tx = lane / hq, ty = lane - tx * hq;
             float ar = 0.f, ai = 0.f;
-            for (int b = 0; b < L; ++b) {
-                const float2 r = R[b * 9 + su], q = s_E[b * ns + sv + t0];
-                ar = fmaf(r.x, q.x, fmaf(-r.y, q.y, ar));
-                ai = fmaf(r.x, q.y, fmaf(r.y, q.x, ai));
+#pragma unroll 4
+            for (int b = 0; b < Q; ++b) {
+                const float wt = s_wc[b * BUILD_WS + ty];
+                const float2 r = R[b * BUILD_TQ + tx];
+                ar = fmaf(wt, r.x, ar);
+                ai = fmaf(wt, r.y, ai);
             }
-            Kw[su * 9 + sv] = make_float2(ar * invL2, ai * invL2);
+            Kq[tx * BUILD_TQ + ty] = make_float2(ar * invL2, ai * invL2);
         }
         __syncwarp();
-        // 3a. A[su][b] = sum_sv K[su][sv] w_v[b - sv]
+        // 3a. A[su][b] = sum_sv K(su - h, sv - h) w_v[b - sv]
         for (int e = lane; e < Sw * S; e += 32) {
             const int su = e / S, b = e - su * S;
+            const float2* Kr = Kq + abs(su - h) * BUILD_TQ;
             float ar = 0.f, ai = 0.f;
             for (int sv = 0; sv < Sw; ++sv) {
                 const int i = b - sv;
                 if (i >= 0 && i < A.J) {
                     const float wv = taps[16 + i];
-                    ar = fmaf(Kw[su * 9 + sv].x, wv, ar);
-                    ai = fmaf(Kw[su * 9 + sv].y, wv, ai);
+                    const float2 kv = Kr[abs(sv - h)];
+                    ar = fmaf(kv.x, wv, ar);
+                    ai = fmaf(kv.y, wv, ai);
                 }
             }
             Ab[su * 19 + b] = make_float2(ar, ai);
@@ -706,11 +795,11 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
     if (lane == 0) atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
 }
 
-size_t gbuild_smem(int L, int hmax) {
-    const int ns = 2 * hmax + 1;
-    const int per_warp = L * 9 + 81 + 9 * 19 + 16;
-    return (size_t)(L * L + 2 * L + 96) * sizeof(float) + (size_t)L * ns * sizeof(float2) +
-           (size_t)BUILD_WARPS * per_warp * sizeof(float2);
+size_t gbuild_smem(int L, int /*hmax*/) {
+    const int Q = L / 2 + 1;
+    const int tabf = (Q * BUILD_WS + Q * Q + 2 * Q + 96 + 1) & ~1;
+    const int per_warp = Q * BUILD_TQ + BUILD_TQ * BUILD_TQ + 9 * 19 + 16;
+    return (size_t)tabf * sizeof(float) + (size_t)BUILD_WARPS * per_warp * sizeof(float2);
 }
 
 void launch_gbuild(const rimo_plan* p, cudaStream_t s) { launch_gbuild_range(p, 0, p->M, s); }
@@ -726,7 +815,7 @@ void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t
     A.wk_dn = p->tab.wk_dn;
     A.tau_x = p->tab.wk_tau_x;
     A.tau_y = p->tab.wk_tau_y;
-    A.E = p->tab.wk_E;
+    A.wc = p->tab.wk_wc;
     A.kb_coef = p->tab.kb_coef;
     A.kb_nterm = p->tab.kb_nterm;
     A.L = p->L;
@@ -737,13 +826,15 @@ void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t
     A.nvis = n;
     A.fx = p->d_fx;
     const size_t sm = gbuild_smem(p->L, p->hmax);
-    RIMO_CUDA(cudaFuncSetAttribute(gbuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    void (*kern)(BuildArgs) = p->L == 16 ? gbuild_kernel<16> : p->L == 32 ? gbuild_kernel<32>
+                            : p->L == 64 ? gbuild_kernel<64> : gbuild_kernel<128>;
+    RIMO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int dev = 0, nsm = 0;
     RIMO_CUDA(cudaGetDevice(&dev));
     RIMO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int64_t blocks = (n + BUILD_WARPS - 1) / BUILD_WARPS;
-    blocks = std::min<int64_t>(blocks, (int64_t)nsm * 8);
-    gbuild_kernel<<<(int)blocks, BUILD_WARPS * 32, sm, s>>>(A);
+    blocks = std::min<int64_t>(blocks, (int64_t)nsm * 16);
+    kern<<<(int)blocks, BUILD_WARPS * 32, sm, s>>>(A);
 }
 
 }  // namespace rimo

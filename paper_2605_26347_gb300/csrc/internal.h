@@ -82,10 +82,11 @@ struct DevTables {
     float4* zq = nullptr;      // [|i_c|][|j_c|], (ny/2+1) x (nx/2+1): sqrt(1-l^2-m^2)-1 as a float pair, |Z_p|
     float* kb_coef = nullptr;  // Horner coefficients of KB(t) in rho = 1 - (2t/J)^2
     int kb_nterm = 0;
-    float* wk_dn = nullptr;    // w-kernel grid: (sqrt(1-lam^2-mu^2)-1), L x L (float)
-    float* wk_tau_x = nullptr; // taper along lam
-    float* wk_tau_y = nullptr; // taper along mu
-    float2* wk_E = nullptr;    // E[a][t + hmax] = e^{+2 pi i t (a - L/2) / L}, L x (2 hmax + 1)
+    // w-kernel grid folded over the signs of (lam, mu): a', b' in [0, L/2], lam = a' 2 fov_x / L
+    float* wk_dn = nullptr;    // sqrt(1 - lam^2 - mu^2) - 1, (L/2 + 1)^2
+    float* wk_tau_x = nullptr; // taper along lam, L/2 + 1
+    float* wk_tau_y = nullptr; // taper along mu, L/2 + 1
+    float* wk_wc = nullptr;    // w(a', t) = m(a') cos(2 pi a' t / L), m = 1 at a' = 0, L/2 else 2; (L/2 + 1) x 8 (t in [0, 4])
 };
 
 }  // namespace rimo

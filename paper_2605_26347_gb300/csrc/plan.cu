@@ -185,35 +185,37 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
     }
     p->tab.kb_nterm = (int)coef.size();
     p->tab.kb_coef = upload(p, coef, s);
-    // residual w-kernel sampling grid over twice the field of view (Section 3.1, Fig. 1)
-    std::vector<float> wdn((size_t)L * L), tx(L), ty(L);
+    // residual w-kernel sampling grid over twice the field of view (Section 3.1, Fig. 1),
+    // folded over the signs of (lam, mu): the chirp is even in both, the edge -L/2 is kept
+    // once as a' = L/2 (same |lam|)
+    const int Q = L / 2 + 1;
+    std::vector<float> wdn((size_t)Q * Q), tx(Q), ty(Q);
     auto taper = [](double lam, double fov) {
         double a = std::fabs(lam), half = 0.5 * fov;
         return a <= half ? 1.0 : 0.54 + 0.46 * std::cos(M_PI * (a - half) / half);
     };
-    for (int a = 0; a < L; ++a) {
-        double lam = (a - L / 2) * (2.0 * p->prm.fov_x / L);
-        double mu = (a - L / 2) * (2.0 * p->prm.fov_y / L);
+    for (int a = 0; a < Q; ++a) {
+        double lam = a * (2.0 * p->prm.fov_x / L);
+        double mu = a * (2.0 * p->prm.fov_y / L);
         tx[a] = (float)taper(lam, p->prm.fov_x);
         ty[a] = (float)taper(mu, p->prm.fov_y);
     }
-    for (int a = 0; a < L; ++a)
-        for (int b = 0; b < L; ++b) {
-            double lam = (a - L / 2) * (2.0 * p->prm.fov_x / L);
-            double mu = (b - L / 2) * (2.0 * p->prm.fov_y / L);
-            wdn[(size_t)a * L + b] = (float)planner::dn(lam, mu);
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) {
+            double lam = a * (2.0 * p->prm.fov_x / L);
+            double mu = b * (2.0 * p->prm.fov_y / L);
+            wdn[(size_t)a * Q + b] = (float)planner::dn(lam, mu);
         }
-    const int ns = 2 * p->hmax + 1;
-    std::vector<float2> E((size_t)L * ns);
-    for (int a = 0; a < L; ++a)
-        for (int t = 0; t < ns; ++t) {
-            double ang = 2.0 * M_PI * (double)(t - p->hmax) * (double)(a - L / 2) / (double)L;
-            E[(size_t)a * ns + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    std::vector<float> wc((size_t)Q * 8, 0.f);  // rows of 8, offsets t in [0, 4]
+    for (int a = 0; a < Q; ++a)
+        for (int t = 0; t < 5; ++t) {
+            const double m = (a == 0 || a == L / 2) ? 1.0 : 2.0;
+            wc[(size_t)a * 8 + t] = (float)(m * std::cos(2.0 * M_PI * (double)a * (double)t / (double)L));
         }
     p->tab.wk_dn = upload(p, wdn, s);
     p->tab.wk_tau_x = upload(p, tx, s);
     p->tab.wk_tau_y = upload(p, ty, s);
-    p->tab.wk_E = upload(p, E, s);
+    p->tab.wk_wc = upload(p, wc, s);
 }
 
 // ---------------------------------------------------------------------------
