@@ -70,11 +70,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-constexpr int GTG_CONSUMERS = 16;                        // consumer warps
+constexpr int GTG_CONSUMERS = GTG_CHUNK;                 // consumer warps
 constexpr int GTG_THREADS = (GTG_CONSUMERS + 1) * 32;   // + one producer warp
 constexpr int GTG_NBUF = 4;   // maximum depth of the tap ring (the plan may use fewer)
 constexpr int GTG_HDR = 256;  // shared-memory header: the ring's and the X buffers' mbarriers
-constexpr int GTG_CV = 16;    // visibilities per chunk (one per consumer warp when de-gridding)
+constexpr int GTG_CV = GTG_CHUNK;  // visibilities per chunk (one per consumer warp)
 
 struct GtgArgs {
     const TileDesc* units;  // this bin's work units, in patch-slot order
@@ -138,10 +138,11 @@ __device__ __forceinline__ void fx_scale(float maxterm, int64_t n, float& s1, fl
 //             32-bit integer reductions.
 // Both parity classes of lanes reduce with four butterfly steps; one more exchange gives
 // every lane y.  Taps stay in registers between the two steps when S <= 16.
-template <int S, int MODE>
+template <int S, int MODE, int PWC>  // PWC: the patch side when known at compile time, else 0
 __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const float2* __restrict__ Xs,
-                                         int* Ahi, int* Alo, float s1, int pbase, int PW, int lane, uint32_t orig,
+                                         int* Ahi, int* Alo, float s1, int pbase, int PWr, int lane, uint32_t orig,
                                          const float2* __restrict__ y_in, float2* __restrict__ y_out) {
+    const int PW = PWC > 0 ? PWC : PWr;  // compile-time row strides fold into the address offsets
     constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
     constexpr int RPI = S <= 8 ? 2 : 1;         // tap rows per instruction
     constexpr int CW = 16 / RPI;                // cells per row and instruction
@@ -213,20 +214,20 @@ __device__ __forceinline__ void vis_tile(const float2* __restrict__ T, const flo
     }
 }
 
-template <int MODE>
+template <int MODE, int PWC>
 __device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float2* Xs, int* Ahi, int* Alo, float s1,
                                              int pbase, int PW, int lane, uint32_t orig, const float2* y_in,
                                              float2* y_out) {
     switch (S) {
-        case 3: vis_tile<3, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 5: vis_tile<5, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 7: vis_tile<7, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 9: vis_tile<9, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 11: vis_tile<11, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 13: vis_tile<13, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 15: vis_tile<15, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        case 17: vis_tile<17, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
-        default: vis_tile<19, MODE>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 3: vis_tile<3, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 5: vis_tile<5, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 7: vis_tile<7, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 9: vis_tile<9, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 11: vis_tile<11, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 13: vis_tile<13, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 15: vis_tile<15, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        case 17: vis_tile<17, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
+        default: vis_tile<19, MODE, PWC>(T, Xs, Ahi, Alo, s1, pbase, PW, lane, orig, y_in, y_out); break;
     }
 }
 
@@ -240,7 +241,9 @@ __device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float
 //                   (shared-memory reductions, one tap row per instruction:
 //                   visibilities of different warps may overlap); then arrive on empty[b].
 // Only unit boundaries (patch load / store) synchronise all consumers.
-template <int MODE>  // 0: de-grid (y_out), 1: grid (y_in), 2: fused de-grid + grid
+// MODE 0: de-grid (y_out), 1: grid (y_in), 2: fused de-grid + grid; PWC: the patch side
+// when known at compile time (the common plans), else 0
+template <int MODE, int PWC>
 __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -248,9 +251,9 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     uint64_t* empty = full + GTG_NBUF;
     uint64_t* xfull = empty + GTG_NBUF;  // [2] X patch buffer landed
     uint64_t* xfree = xfull + 2;         // [2] consumers are done with the buffer
-    VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + GTG_HDR);      // GTG_NBUF x 16 entries
+    VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + GTG_HDR);      // GTG_NBUF x GTG_CV entries
     float2* taps = reinterpret_cast<float2*>(smraw + GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta));
-    const int PW = A.PW, npatch = PW * PW;
+    const int PW = PWC > 0 ? PWC : A.PW, npatch = PW * PW;
     const int chunk_f2 = A.chunk_bytes / 8;
     const uint32_t NB = (uint32_t)A.nbuf;
     const bool pre = GATHER && A.prefetch;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 const VisMeta mt = mring[b * GTG_CV + warp];
                 const int du = mt.pos & 255, dv = (mt.pos >> 8) & 255, S = (mt.pos >> 16) & 255;
                 const int loc = (int)(mt.off - mring[b * GTG_CV].off);
-                vis_dispatch<MODE>(S, taps + (size_t)b * chunk_f2 + loc, Xs, Ahi, Alo, s1, du * PW + dv, PW, lane,
+                vis_dispatch<MODE, PWC>(S, taps + (size_t)b * chunk_f2 + loc, Xs, Ahi, Alo, s1, du * PW + dv, PW, lane,
                                    mt.orig, A.y_in, A.y_out);
             }
             __syncwarp();
@@ -491,9 +494,12 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf, A.prefetch) > limit) --A.nbuf;
     const size_t sm = gtg_smem(p, MODE, A.nbuf, A.prefetch);
     if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
-    RIMO_CUDA(cudaFuncSetAttribute(gtg_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // patch sides of the uv-tiles 32 and 64 with 15 x 15 tiles are compile-time constants
+    void (*kern)(GtgArgs) = p->PW == 46 ? gtg_kernel<MODE, 46> : p->PW == 78 ? gtg_kernel<MODE, 78>
+                                                                              : gtg_kernel<MODE, 0>;
+    RIMO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nu, p->n_sm);
-    gtg_kernel<MODE><<<grid, GTG_THREADS, sm, s>>>(A);
+    kern<<<grid, GTG_THREADS, sm, s>>>(A);
     if (MODE != 0 && br.m1 > br.m0)
         merge_patches_kernel<<<br.m1 - br.m0, 256, 0, s>>>(p->d_patch, p->d_merge + br.m0, p->PW * p->PW);
 }

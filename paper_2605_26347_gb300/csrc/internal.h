@@ -10,6 +10,8 @@
 #include "rimo.h"
 
 namespace rimo {
+// visibilities per tap-ring chunk of the grid step, one per consumer warp
+constexpr int GTG_CHUNK = 20;
 
 // ---------------------------------------------------------------------------
 // Error handling: every public entry point catches rimo::Error and returns its status.
@@ -128,7 +130,7 @@ struct rimo_plan {
     int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)
     int32_t* d_status = nullptr;   // device-side error flag (bounded waits)
     uint32_t* d_fx = nullptr;      // fixed-point grid-step bounds (layout: rimo::FX_*)
-    int max_tiles_bin = 0, chunk_vis = 16, chunk_bytes = 0, nbuf = 4, n_sm = 0;
+    int max_tiles_bin = 0, chunk_vis = rimo::GTG_CHUNK, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
 

@@ -351,16 +351,16 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
             x.r = std::sqrt(cu * cu + cv * cv);
             // Interleave the tile's visibilities (arrival order within a tile is time, so
             // neighbours are the same few baselines a fraction of a cell apart): viewed
-            // as 16 rows of nc, the new order reads the list column by column, so that
-            // any 16 consecutive visibilities - one ring chunk, de-gridded and gridded
-            // at the same time by 16 warps - come from 16 far-apart instants and rarely
-            // update the same grid cells.
+            // as GTG_CHUNK rows of nc, the new order reads the list column by column, so
+            // that the GTG_CHUNK consecutive visibilities of one ring chunk, de-gridded and
+            // gridded at the same time by as many warps, come from far-apart instants and
+            // rarely update the same grid cells.
             {
-                const int64_t n = x.ve - x.vb, nc = (n + 15) / 16;
+                const int64_t n = x.ve - x.vb, nc = (n + GTG_CHUNK - 1) / GTG_CHUNK;
                 tmp.assign(order.begin() + x.vb, order.begin() + x.ve);
                 int64_t o = x.vb;
                 for (int64_t c = 0; c < nc; ++c)
-                    for (int64_t r = 0; r < 16; ++r)
+                    for (int64_t r = 0; r < GTG_CHUNK; ++r)
                         if (r * nc + c < n) order[o++] = tmp[r * nc + c];
             }
             x.bytes = 0;
@@ -478,13 +478,13 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     // ---- device
     build_tables(p, s);
     p->d_meta = upload(p, meta, s);
-    // chunk descriptors: 16 consecutive visibilities of a unit share one tap range
+    // chunk descriptors: GTG_CHUNK consecutive visibilities of a unit share one tap range
     {
         std::vector<ChunkDesc> ch;
         for (auto& u : p->tiles_host) {
             u.cb = (int64_t)ch.size();
-            for (int64_t v0 = u.vb; v0 < u.ve; v0 += 16) {
-                const int64_t v1 = std::min(u.ve, v0 + 16);
+            for (int64_t v0 = u.vb; v0 < u.ve; v0 += GTG_CHUNK) {
+                const int64_t v1 = std::min<int64_t>(u.ve, v0 + GTG_CHUNK);
                 const VisMeta& m0 = meta[v0];
                 const VisMeta& m1 = meta[v1 - 1];
                 const int64_t S1 = (m1.pos >> 16) & 255;
@@ -559,7 +559,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         RIMO_CUDA(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
         p->device = dev;
         const int s2 = p->max_S * p->max_S;
-        p->chunk_vis = 16;
+        p->chunk_vis = GTG_CHUNK;
         p->chunk_bytes = p->chunk_vis * (s2 + (s2 & 1)) * (int)sizeof(float2);
     }
     p->d_AB = (float2*)dev_alloc(p, (size_t)2 * p->nx * p->ny * sizeof(float2));
