@@ -16,6 +16,7 @@
 // 2N-point inverse DFT kept on N centred outputs is two N-point inverse DFTs of folded
 // inputs (even and odd outputs).  Each N-point DFT is a Stockham radix-16 FFT held in
 // registers (16 points per thread, N/16 threads), exchanging through shared memory.
+#include <cstring>
 #include <cstdio>
 
 #include <map>
@@ -326,7 +327,7 @@ __device__ __forceinline__ float2 dsmem_ld2(uint32_t addr) {
 // distributed shared memory (64-byte writes for C RB = 8).
 template <int RB, int C, int SR, int NK, int THREADS, class Src, class Dst>
 __device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst, float2* out, size_t ld,
-                                                 int r0_block) {
+                                                 int r0_block) {  // r0_block: this CTA's first row
     if constexpr (C == 1) {
         __syncthreads();
         constexpr int NP = RB / 2;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst,
         constexpr int NP = C * RB / 2, KPC = NK / C;
         static_assert(THREADS % NP == 0, "a thread keeps one row pair");
         const int rank = (int)(blockIdx.x % C);
-        const int rbase = (int)(blockIdx.x - rank) * RB;  // first row of the cluster
+        const int rbase = r0_block - rank * RB;  // first row of the cluster
         const int q = threadIdx.x % NP;                   // rows 2q, 2q + 1 of the cluster
         const uint32_t b0 = dsmem_map(smem + ((2 * q) % RB) * SR, (2 * q) / RB);
         const uint32_t b1 = dsmem_map(smem + ((2 * q + 1) % RB) * SR, (2 * q + 1) / RB);
@@ -390,6 +391,23 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
                                                (size_t)ny, (int)blockIdx.x * RB);
 }
 
+// ----------------------------------------------------------------------------- row selection
+// The column passes transform only the grid rows u of uv-tile rows holding a needed tile
+// (tiles no footprint of the bin reaches are neither stored nor read): block b takes rows
+// [row[b / bpt] * RG bpt + (b % bpt) RG, + RG), bpt = TS / RG blocks per tile row.  A
+// cluster's blocks stay within one tile row (bpt is a multiple of C).  With on = 0 block b
+// takes rows [b RG, + RG).  `bits` marks the selected tile rows for the last pass.
+struct RowSel {
+    int on, bpt, shift;
+    uint32_t bits[8];
+    uint16_t row[256];
+};
+
+__device__ __forceinline__ int sel_row0(const RowSel& sel, int rows_per_blk) {
+    const int b = (int)blockIdx.x;
+    return sel.on ? ((int)sel.row[b / sel.bpt] * sel.bpt + b % sel.bpt) * rows_per_blk : b * rows_per_blk;
+}
+
 // ----------------------------------------------------------------------------- forward cols
 // grid: gx / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
 // need[tu * ntv + tv] != 0 marks the tiles of X some active patch reads; the rest of X is
@@ -397,18 +415,19 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
 template <int N, int RG>
 __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
     fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X, const uint8_t* __restrict__ need,
-                    int shift, const float2* __restrict__ tws) {
+                    int shift, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int ntv = L >> shift;
     uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RG * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const size_t u = (size_t)blockIdx.x * RG + g;
+    const int r0 = sel_row0(sel, RG);
+    const size_t u = (size_t)r0 + g;
     const float2* in = At + u * N;
     float2* out = X + u * L;
     for (int e = threadIdx.x; e < RG * ntv; e += blockDim.x) {
-        const size_t uu = (size_t)blockIdx.x * RG + e / ntv;
+        const size_t uu = (size_t)r0 + e / ntv;
         s_need[e] = need[(uu >> shift) * ntv + e % ntv];
     }
     float2 v[16];
@@ -468,16 +487,17 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs F) {
 template <int N, int RB, int C>
 __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
     inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B, int gx, const uint8_t* __restrict__ need,
-                    int shift, const float2* __restrict__ tws) {
+                    int shift, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int ntv = L >> shift;
     uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RB * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const int u = blockIdx.x * RB + g;
+    const int r0 = sel_row0(sel, RB);
+    const int u = r0 + g;
     for (int e = threadIdx.x; e < RB * ntv; e += blockDim.x) {
-        const int uu = blockIdx.x * RB + e / ntv;
+        const int uu = r0 + e / ntv;
         s_need[e] = need[(size_t)(uu >> shift) * ntv + e % ntv];
     }
     __syncthreads();
@@ -494,7 +514,7 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
     // kept output kk < N: k = kk (kk < N/2) or kk + N; image row i = (k < N/2 ? k : k - L) + N/2
     transposed_store<RB, C, SR, N, RB * N / 8>(
         smem, [](int kk) { return kk < N / 2 ? kk : kk + N; },
-        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, B, (size_t)gx, (int)blockIdx.x * RB);
+        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, B, (size_t)gx, r0);
 }
 
 // ----------------------------------------------------------------------------- inverse rows
@@ -502,7 +522,7 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
 template <int N, int RG>
 __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
     inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out, int ny, ZArgs z, int accumulate,
-                    int real_only, const float2* __restrict__ tws) {
+                    int real_only, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
@@ -512,8 +532,18 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
     const float2* in = B + (size_t)i * L;
     float2* orow = out + (size_t)i * N;
     float2 v[16];
+    // columns u of tile rows the inverse column pass skipped are zero (not stored)
+    uint32_t keep = 0xffffu;
+    if (sel.on) {
+        keep = 0;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = __ldg(&in[t + T * m]);
+        for (int m = 0; m < 16; ++m) {
+            const int tr = (t + T * m) >> sel.shift;
+            keep |= ((sel.bits[tr >> 5] >> (tr & 31)) & 1u) << m;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = (keep >> m) & 1u ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
     fft_n<L, true>(v, sm, t, tws);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -613,6 +643,32 @@ static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, c
     }
 }
 
+// Row selection of `bin` for blocks of rpb rows (off when a block would span tile rows)
+static RowSel row_sel(const rimo_plan* p, int bin, int rpb) {
+    RowSel r;
+    std::memset(&r, 0, sizeof(r));
+    const auto& tr = p->trows[bin];
+    const int ntu = p->gx / p->TS;
+    if (rpb > p->TS || ntu > 256) return r;
+    r.on = 1;
+    r.bpt = p->TS / rpb;
+    r.shift = p->TS == 64 ? 6 : 5;
+    for (size_t i = 0; i < tr.size(); ++i) {
+        r.row[i] = tr[i];
+        r.bits[tr[i] >> 5] |= 1u << (tr[i] & 31);
+    }
+    return r;
+}
+static int sel_blocks(const rimo_plan* p, int bin, const RowSel& r, int rpb) {
+    return r.on ? (int)p->trows[bin].size() * r.bpt : p->gx / rpb;
+}
+// the inverse column pass's selection (blocks of RB rows, clusters of C blocks; transform
+// length 2 ny), shared with the inverse row pass that reads its output
+static RowSel inv_sel(const rimo_plan* p, int bin) {
+    const int RB = 4096 / p->ny, C = RB >= 8 ? 1 : 8 / RB;
+    return row_sel(p, bin, C * RB <= p->TS ? RB : p->TS + 1);
+}
+
 template <int N>
 static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
     constexpr int RG = rows_per_block<N>();
@@ -620,8 +676,11 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
     const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
     set_smem(fwd_cols_kernel<N, RG>, sm);
     const size_t ntile = (size_t)(p->gx / p->TS) * (p->gy / p->TS);
-    fwd_cols_kernel<N, RG><<<p->gx / RG, RG * N / 8, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
-                                                               p->TS == 64 ? 6 : 5, p->tab.tws_y);
+    const RowSel sel = row_sel(p, bin, RG);
+    const int grid = sel_blocks(p, bin, sel, RG);
+    if (grid == 0) return;
+    fwd_cols_kernel<N, RG><<<grid, RG * N / 8, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
+                                                        p->TS == 64 ? 6 : 5, p->tab.tws_y, sel);
 }
 
 template <int N>
@@ -648,16 +707,20 @@ static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStre
         F.gy = p->gy;
         fold_kernel<<<br.n1 - br.n0, 256, 0, s>>>(F);
     }
-    const int grid = p->gx / RB, shift = p->TS == 64 ? 6 : 5;
+    const int shift = p->TS == 64 ? 6 : 5;
     const uint8_t* need = p->d_need + (size_t)bin * ntile;
+    // C consecutive blocks of a cluster stay in one tile row: TS / RB is a multiple of C
+    const RowSel sel = inv_sel(p, bin);
+    const int grid = sel_blocks(p, bin, sel, RB);
+    if (grid == 0) return;
     if constexpr (C > 1) {
         if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
         set_smem(inv_cols_kernel<N, RB, C>, sm);
         launch_clustered(inv_cols_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, (const float2*)p->d_X, B, p->gx,
-                         need, shift, (const float2*)p->tab.tws_y);
+                         need, shift, (const float2*)p->tab.tws_y, sel);
     } else {
         set_smem(inv_cols_kernel<N, RB, 1>, sm);
-        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tws_y);
+        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tws_y, sel);
     }
 }
 
@@ -667,7 +730,8 @@ static void inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, 
     constexpr int RG = rows_per_block<N>();
     const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2);
     set_smem(inv_rows_kernel<N, RG>, sm);
-    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 8, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re, p->tab.tws_x);
+    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 8, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re, p->tab.tws_x,
+                                                            inv_sel(p, bin));
 }
 
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {

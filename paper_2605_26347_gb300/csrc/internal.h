@@ -133,6 +133,7 @@ struct rimo_plan {
     int max_tiles_bin = 0, chunk_vis = rimo::GTG_CHUNK, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
+    std::vector<std::vector<uint16_t>> trows;  // per bin: uv-tile rows (tu) holding a needed tile
 
     // kernel surrogate (mode RIMO_MODE_SURROGATE) or exact on-the-fly tiles (mode
     // RIMO_MODE_ONTHEFLY): tiles generated per bin at apply time

@@ -546,6 +546,15 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         }
         p->d_need_list = upload(p, nl, s);
         p->need_host = nl;
+        // tile rows with a needed tile: the column passes transform only their grid rows
+        p->trows.assign(P, {});
+        for (int b = 0; b < P; ++b)
+            for (int tu = 0; tu < ntu; ++tu)
+                for (int tv = 0; tv < ntv; ++tv)
+                    if (need[(size_t)b * ntile + (size_t)tu * ntv + tv]) {
+                        p->trows[b].push_back((uint16_t)tu);
+                        break;
+                    }
     }
     p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
