@@ -322,17 +322,18 @@ __device__ __forceinline__ float2 dsmem_ld2(uint32_t addr) {
 
 // Transposed store of a CTA's (C = 1) or a cluster's (C > 1) rows: output row dst(kk) of
 // `out` (leading dimension ld) gets, at columns [r0, r0 + C RB), value src(kk) of each of
-// the C RB rows, for the nk kept values kk.  With C > 1, after a cluster barrier each CTA
+// the C RB rows, for the nk kept values kk with keep(kk) (the others are not written).  With C > 1, after a cluster barrier each CTA
 // writes nk / C of them for all the cluster's rows, reading partners' rows through
 // distributed shared memory (64-byte writes for C RB = 8).
-template <int RB, int C, int SR, int NK, int THREADS, class Src, class Dst>
-__device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst, float2* out, size_t ld,
+template <int RB, int C, int SR, int NK, int THREADS, class Src, class Dst, class Keep>
+__device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst, Keep keep, float2* out, size_t ld,
                                                  int r0_block) {  // r0_block: this CTA's first row
     if constexpr (C == 1) {
         __syncthreads();
         constexpr int NP = RB / 2;
         for (int e = threadIdx.x; e < NK * NP; e += THREADS) {
             const int kk = e / NP, q = e % NP;
+            if (!keep(kk)) continue;
             const int k = src(kk);
             const float2 a = smem[(2 * q) * SR + pidx(k)], b = smem[(2 * q + 1) * SR + pidx(k)];
             *reinterpret_cast<float4*>(&out[(size_t)dst(kk) * ld + r0_block + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
@@ -349,12 +350,30 @@ __device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst,
         const uint32_t b1 = dsmem_map(smem + ((2 * q + 1) % RB) * SR, (2 * q + 1) / RB);
         for (int e = threadIdx.x; e < KPC * NP; e += THREADS) {
             const int kk = rank * KPC + e / NP;
+            if (!keep(kk)) continue;
             const uint32_t off = (uint32_t)pidx(src(kk)) * 8u;
             const float2 a = dsmem_ld2(b0 + off), b = dsmem_ld2(b1 + off);
             *reinterpret_cast<float4*>(&out[(size_t)dst(kk) * ld + rbase + 2 * q]) = make_float4(a.x, a.y, b.x, b.y);
         }
         cluster_sync_relaxed();  // partners are done reading before the block may exit
     }
+}
+
+// ----------------------------------------------------------------------------- row selection
+// The column passes transform only the grid rows u of uv-tile rows holding a needed tile
+// (tiles no footprint of the bin reaches are neither stored nor read): block b takes rows
+// [row[b / bpt] * RG bpt + (b % bpt) RG, + RG), bpt = TS / RG blocks per tile row.  A
+// cluster's blocks stay within one tile row (bpt is a multiple of C).  With on = 0 block b
+// takes rows [b RG, + RG).  `bits` marks the selected tile rows for the last pass.
+struct RowSel {
+    int on, bpt, shift;
+    uint32_t bits[8];
+    uint16_t row[256];
+};
+
+__device__ __forceinline__ int sel_row0(const RowSel& sel, int rows_per_blk) {
+    const int b = (int)blockIdx.x;
+    return sel.on ? ((int)sel.row[b / sel.bpt] * sel.bpt + b % sel.bpt) * rows_per_blk : b * rows_per_blk;
 }
 
 // ----------------------------------------------------------------------------- forward rows
@@ -364,7 +383,7 @@ __device__ __forceinline__ void transposed_store(float2* smem, Src src, Dst dst,
 template <int N, int RB, int C>
 __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
     fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At, int ny, ZArgs z,
-                    const float2* __restrict__ tws) {
+                    const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
@@ -387,25 +406,11 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
     fft_n<L, false>(v, sm, t, tws);
 #pragma unroll
     for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<L>(m)];
-    transposed_store<RB, C, SR, L, RB * N / 8>(smem, [](int kk) { return kk; }, [](int kk) { return kk; }, At,
-                                               (size_t)ny, (int)blockIdx.x * RB);
-}
-
-// ----------------------------------------------------------------------------- row selection
-// The column passes transform only the grid rows u of uv-tile rows holding a needed tile
-// (tiles no footprint of the bin reaches are neither stored nor read): block b takes rows
-// [row[b / bpt] * RG bpt + (b % bpt) RG, + RG), bpt = TS / RG blocks per tile row.  A
-// cluster's blocks stay within one tile row (bpt is a multiple of C).  With on = 0 block b
-// takes rows [b RG, + RG).  `bits` marks the selected tile rows for the last pass.
-struct RowSel {
-    int on, bpt, shift;
-    uint32_t bits[8];
-    uint16_t row[256];
-};
-
-__device__ __forceinline__ int sel_row0(const RowSel& sel, int rows_per_blk) {
-    const int b = (int)blockIdx.x;
-    return sel.on ? ((int)sel.row[b / sel.bpt] * sel.bpt + b % sel.bpt) * rows_per_blk : b * rows_per_blk;
+    // rows k of At the forward column pass does not transform are not stored
+    transposed_store<RB, C, SR, L, RB * N / 8>(
+        smem, [](int kk) { return kk; }, [](int kk) { return kk; },
+        [&](int kk) { return !sel.on || ((sel.bits[(kk >> sel.shift) >> 5] >> ((kk >> sel.shift) & 31)) & 1u); },
+        At, (size_t)ny, (int)blockIdx.x * RB);
 }
 
 // ----------------------------------------------------------------------------- forward cols
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
     // kept output kk < N: k = kk (kk < N/2) or kk + N; image row i = (k < N/2 ? k : k - L) + N/2
     transposed_store<RB, C, SR, N, RB * N / 8>(
         smem, [](int kk) { return kk < N / 2 ? kk : kk + N; },
-        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, B, (size_t)gx, r0);
+        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, [](int) { return true; }, B, (size_t)gx, r0);
 }
 
 // ----------------------------------------------------------------------------- inverse rows
@@ -626,23 +631,6 @@ static void set_smem(K kernel, size_t bytes) {
         default: fail(RIMO_ERR_INVALID_ARG, "unsupported transform length");           \
     }
 
-template <int N>
-static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
-    constexpr int RB = rows_per_block<N>();
-    constexpr int C = cluster_of<RB>();
-    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2);
-    const int grid = p->ny / RB;
-    if constexpr (C > 1) {
-        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "image rows do not fill the transposed-store clusters");
-        set_smem(fwd_rows_kernel<N, RB, C>, sm);
-        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, x, At, p->ny, zargs(p, bin),
-                         (const float2*)p->tab.tws_x);
-    } else {
-        set_smem(fwd_rows_kernel<N, RB, 1>, sm);
-        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tws_x);
-    }
-}
-
 // Row selection of `bin` for blocks of rpb rows (off when a block would span tile rows)
 static RowSel row_sel(const rimo_plan* p, int bin, int rpb) {
     RowSel r;
@@ -662,11 +650,32 @@ static RowSel row_sel(const rimo_plan* p, int bin, int rpb) {
 static int sel_blocks(const rimo_plan* p, int bin, const RowSel& r, int rpb) {
     return r.on ? (int)p->trows[bin].size() * r.bpt : p->gx / rpb;
 }
+// the forward column pass's selection (blocks of 4096 / ny rows), shared with the forward
+// row pass that writes its input
+static RowSel fwd_sel(const rimo_plan* p, int bin) { return row_sel(p, bin, 4096 / p->ny); }
 // the inverse column pass's selection (blocks of RB rows, clusters of C blocks; transform
 // length 2 ny), shared with the inverse row pass that reads its output
 static RowSel inv_sel(const rimo_plan* p, int bin) {
     const int RB = 4096 / p->ny, C = RB >= 8 ? 1 : 8 / RB;
     return row_sel(p, bin, C * RB <= p->TS ? RB : p->TS + 1);
+}
+
+template <int N>
+static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
+    constexpr int RB = rows_per_block<N>();
+    constexpr int C = cluster_of<RB>();
+    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2);
+    const int grid = p->ny / RB;
+    if constexpr (C > 1) {
+        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "image rows do not fill the transposed-store clusters");
+        set_smem(fwd_rows_kernel<N, RB, C>, sm);
+        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, x, At, p->ny, zargs(p, bin),
+                         (const float2*)p->tab.tws_x, fwd_sel(p, bin));
+    } else {
+        set_smem(fwd_rows_kernel<N, RB, 1>, sm);
+        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tws_x,
+                                                               fwd_sel(p, bin));
+    }
 }
 
 template <int N>
@@ -676,7 +685,7 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
     const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
     set_smem(fwd_cols_kernel<N, RG>, sm);
     const size_t ntile = (size_t)(p->gx / p->TS) * (p->gy / p->TS);
-    const RowSel sel = row_sel(p, bin, RG);
+    const RowSel sel = fwd_sel(p, bin);
     const int grid = sel_blocks(p, bin, sel, RG);
     if (grid == 0) return;
     fwd_cols_kernel<N, RG><<<grid, RG * N / 8, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
