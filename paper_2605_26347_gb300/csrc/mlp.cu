@@ -621,16 +621,29 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
     uint32_t phase = 0;
     bool ok = true;
     const int ntile = (A.n + 127) / 128;
+    // the next tile's inputs are loaded (raw) while this tile computes
+    float in_u = 0.f, in_v = 0.f, in_w = 0.f;
+    int64_t in_off = 0;
+    auto load_inputs = [&](int t) {
+        if (tid < 128 && t < ntile) {
+            const int j = t * 128 + tid < A.n ? t * 128 + tid : A.n - 1;
+            const int64_t k = A.v0 + j;
+            in_u = __ldg(A.phiu + k);
+            in_v = __ldg(A.phiv + k);
+            in_w = __ldg(A.wr + k);
+            in_off = A.meta[k].off;
+        }
+    };
+    load_inputs(blockIdx.x);
     for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
         const int base = tile * 128;
         if (tid < 128) {
-            const int j = base + tid < A.n ? base + tid : A.n - 1;
-            const int64_t k = A.v0 + j;
-            sx[3 * tid + 0] = 2.f * A.phiu[k] - 1.f;
-            sx[3 * tid + 1] = 2.f * A.phiv[k] - 1.f;
-            sx[3 * tid + 2] = A.wr[k] * A.inv_w;
-            soff[tid] = A.meta[k].off;
+            sx[3 * tid + 0] = 2.f * in_u - 1.f;
+            sx[3 * tid + 1] = 2.f * in_v - 1.f;
+            sx[3 * tid + 2] = in_w * A.inv_w;
+            soff[tid] = in_off;
         }
+        load_inputs(tile + gridDim.x);
         __syncthreads();
         {   // layer 1: row r, hidden units [64 h, 64 h + 64)
             const int r = tid & 127, h = tid >> 7;
@@ -669,16 +682,25 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
         {   // layer-2 read-out: row 32 (warp % 4) + lane, columns [64 (warp / 4), + 64)
             const int r = 32 * (warp & 3) + lane;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 16) {
+            for (int c0 = 0; c0 < 64; c0 += 32) {  // two 16-column loads in flight per wait
                 const int col = 64 * (warp >> 2) + c0;
-                float v[16];
-                tc::tmem_ld16(tmem + lane_base + (uint32_t)col, v);
-                uint32_t w[8];
+                uint32_t va[16], vb[16];
+                tc::tmem_ld16_async(tmem + lane_base + (uint32_t)col, va);
+                tc::tmem_ld16_async(tmem + lane_base + (uint32_t)(col + 16), vb);
+                tc::tmem_wait_ld_tied(va);
+                tc::reg_tie(vb);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    w[i] = pack_bf2(gelu_f(v[2 * i] + sb2[col + 2 * i]), gelu_f(v[2 * i + 1] + sb2[col + 2 * i + 1]));
-                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, col, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, col + 8, 128)) = make_uint4(w[4], w[5], w[6], w[7]);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t* v = h ? vb : va;
+                    const int cc = col + 16 * h;
+                    uint32_t w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        w[i] = pack_bf2(gelu_f(__uint_as_float(v[2 * i]) + sb2[cc + 2 * i]),
+                                        gelu_f(__uint_as_float(v[2 * i + 1]) + sb2[cc + 2 * i + 1]));
+                    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, cc, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, cc + 8, 128)) = make_uint4(w[4], w[5], w[6], w[7]);
+                }
             }
         }
         tc::fence_proxy_async();
@@ -707,9 +729,17 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
 #pragma unroll 1
             for (int c = warp >> 2; c < (SUR_TAPS + 15) / 16; c += 2) {
                 const int q0 = 16 * c;
+                uint32_t rr[16], ri[16];
+                tc::tmem_ld16_async(tmem + lane_base + (uint32_t)q0, rr);
+                tc::tmem_ld16_async(tmem + lane_base + (uint32_t)(GEN_IM + q0), ri);
+                tc::tmem_wait_ld_tied(rr);
+                tc::reg_tie(ri);
                 float re[16], im[16];
-                tc::tmem_ld16(tmem + lane_base + (uint32_t)q0, re);
-                tc::tmem_ld16(tmem + lane_base + (uint32_t)(GEN_IM + q0), im);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    re[i] = __uint_as_float(rr[i]);
+                    im[i] = __uint_as_float(ri[i]);
+                }
 #pragma unroll
                 for (int i = 0; i < 16; i += 2) {
                     const int q = q0 + i;
