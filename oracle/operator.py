@@ -9,6 +9,9 @@ Eq. 6: Phi = [Phi_1 ... Phi_P]^T with Phi_p = G_p F Z_p.
          (indices modulo the grid) with weights T_k = w-kernel (*) KB taps.
 Eq. 7 and Eq. 8: Phi^dagger Phi = sum_p Z_p^dagger F^dagger G_p^dagger G_p F Z_p.
 Section 3.3: H_p = G_p^dagger G_p (Hermitian).
+Section 2 (Eq. 3): a data weighting (e.g. Briggs) is applied to the data and injected
+into the model: with weights w the operator is W Phi, W = diag(w), so that Phi^dagger Phi
+becomes Phi^dagger W^2 Phi and H_p becomes G_p^dagger W_p^2 G_p.
 
 This is test infrastructure: only the tests, the smoke check and the
 benchmark's CPU-baseline leg use it.
@@ -58,8 +61,10 @@ class Geometry:
 class Operator:
     """The discrete hybrid w-stacking / w-projection operator of one plan."""
 
-    def __init__(self, uvw: np.ndarray, plan: Plan, build_g: bool = True):
+    def __init__(self, uvw: np.ndarray, plan: Plan, build_g: bool = True, weights=None):
         self.uvw = np.asarray(uvw, dtype=np.float64)
+        # diagonal data weighting W (None: W = I)
+        self.w = None if weights is None else np.asarray(weights, dtype=np.float64)
         self.plan = plan
         pp = plan.params
         self.pp = pp
@@ -160,10 +165,12 @@ class Operator:
                 continue
             X = self.fwd_grid(self.z_layer(p) * x)
             y[rows] = self.G[p] @ X.ravel()
-        return y
+        return y if self.w is None else self.w * y
 
     def phi_adj(self, y: np.ndarray) -> np.ndarray:
         y = np.asarray(y, dtype=np.complex128)
+        if self.w is not None:
+            y = self.w * y
         pp = self.pp
         out = np.zeros((pp.ny, pp.nx), dtype=np.complex128)
         for p in range(self.plan.P):
@@ -184,7 +191,10 @@ class Operator:
                 continue
             Zp = self.z_layer(p)
             X = self.fwd_grid(Zp * x).ravel()
-            Xh = (self.G[p].conj().T @ (self.G[p] @ X)).reshape(self.gx, self.gy)
+            yp = self.G[p] @ X
+            if self.w is not None:
+                yp = self.w[self.plan.bins == p] ** 2 * yp
+            Xh = (self.G[p].conj().T @ yp).reshape(self.gx, self.gy)
             out += np.conj(Zp) * self.adj_grid(Xh)
         return out.real.astype(np.complex128) if real_part_only else out
 
@@ -197,6 +207,8 @@ class Operator:
     def holographic(self, p: int) -> sp.csr_matrix:
         """H_p = G_p^dagger G_p as an N' x N' sparse matrix (Section 3.3)."""
         G = self.G[p]
+        if self.w is not None:
+            G = sp.diags(self.w[self.plan.bins == p]) @ G
         return (G.conj().T @ G).tocsr()
 
     # ---- full-size sampled evaluation --------------------------------------
@@ -224,4 +236,4 @@ class Operator:
             Ev = np.exp(-2j * math.pi * np.outer(cv, ic) / self.gy)   # (S, ny)
             Xs = (Ev @ (zc[p] @ Eu)).T                                 # (S_u, S_v)
             y[q] = np.sum(Ts[q] * Xs)
-        return y
+        return y if self.w is None else self.w[ks] * y
