@@ -135,6 +135,7 @@ typedef struct rimo_plan_info {
     int32_t tile_size;         /* uv-tile edge of the gridding schedule (0: none)  */
     int32_t truncated;         /* 1: at the largest residual w the kernel needs more */
                                /* than max_wsupport taps to keep w_norm_frac         */
+    int32_t weighted;          /* 1: a data weighting is injected (set_weights)    */
 } rimo_plan_info;
 
 typedef struct rimo_plan* rimo_plan_t;
@@ -393,6 +394,32 @@ rimo_status rimo_batch_info(rimo_batch_t batch, int32_t* n_plans, int64_t* captu
  */
 rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
                                void* stream, int32_t* tile_out, double* ms_out);
+
+/*
+ * Data weighting injected into the measurement operator (Section 2, Eq. 3: a weighting
+ * such as Briggs' is applied to the data and injected into the model).  After this call
+ * the plan's operator is W Phi with W = diag(w): Phi returns w_k y_k, Phi^dagger takes
+ * W y, Phi^dagger Phi becomes Phi^dagger W^2 Phi and a holographic matrix built later is
+ * G^dagger W^2 G.  The weights multiply the tiles of G (a stored-G plan rebuilds G on
+ * `stream`; plans that generate tiles multiply them at generation), so an apply costs the
+ * same as without weights.  rimo_plan_get_tiles then returns weighted tiles.
+ * w: host, M values in caller order, finite and >= 0 (copied); NULL removes the weighting.
+ * Errors: INVALID_ARG (null plan, negative or non-finite weight), STATE (the plan's
+ * tiles were already folded into H), CUDA.  Synchronises `stream`.
+ */
+rimo_status rimo_plan_set_weights(rimo_plan_t plan, const float* w, void* stream);
+
+/*
+ * Briggs' robust weights of unit natural weights (the weighting Section 2 cites), on the
+ * image's Fourier grid: nx x ny cells of 1/fov_x x 1/fov_y; visibility k falls in cell
+ * (floor(u_k fov_x + 1/2) mod nx, floor(v_k fov_y + 1/2) mod ny); with D_c the number of
+ * visibilities of cell c, f^2 = (5 10^-robust)^2 M / sum_c D_c^2 and
+ * w_k = 1 / (1 + f^2 D_c(k)).  robust -> +inf gives natural weights (1), -inf uniform.
+ * uvw: host, M x 3 (wavelengths); w_out: host, M floats.  Computed on the host (FP64).
+ * Errors: INVALID_ARG (null pointer, M < 0, nx or ny < 1, non-positive field of view).
+ */
+rimo_status rimo_briggs_weights(const double* uvw, int64_t M, int32_t nx, int32_t ny, double fov_x,
+                                double fov_y, double robust, float* w_out);
 
 /*
  * Kernel surrogate as the plan's tile generator.  A plan created with mode

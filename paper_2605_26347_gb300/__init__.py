@@ -182,6 +182,17 @@ class Plan:
                                                          m.ctypes.data, _stream_ptr(stream)))
         return out
 
+    def set_weights(self, w, stream=None) -> None:
+        """rimo_plan_set_weights: the operator becomes diag(w) Phi (w: M weights, caller
+        order, finite and >= 0; None removes the weighting)."""
+        if w is None:
+            _lib.check(self._lib.rimo_plan_set_weights(self._h, None, _stream_ptr(stream)))
+            return
+        wa = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
+        if wa.size != self.M:
+            raise ValueError(f"expected {self.M} weights, got {wa.size}")
+        _lib.check(self._lib.rimo_plan_set_weights(self._h, wa.ctypes.data, _stream_ptr(stream)))
+
     def set_surrogate(self, sur: "Surrogate") -> None:
         """rimo_plan_set_surrogate: generate this (surrogate-mode) plan's tiles with `sur`."""
         _lib.check(self._lib.rimo_plan_set_surrogate(self._h, sur._h))
@@ -327,6 +338,16 @@ class Batch:
         caps = C.c_int64()
         _lib.check(self._lib.rimo_batch_info(self._h, C.byref(n), C.byref(caps)))
         return {"n_plans": n.value, "captures": caps.value}
+
+
+def briggs_weights(uvw, nx: int, ny: int, fov_x: float, fov_y: float, robust: float) -> np.ndarray:
+    """rimo_briggs_weights: Briggs' robust weights (float32, caller order)."""
+    lib = _lib.load()
+    u = _uvw_arg(uvw)
+    out = np.zeros(u.shape[0], np.float32)
+    _lib.check(lib.rimo_briggs_weights(u.ctypes.data, u.shape[0], int(nx), int(ny), float(fov_x), float(fov_y),
+                                       float(robust), out.ctypes.data))
+    return out
 
 
 def autotune_tile(uvw, params: PlanParams, cache_path: str | None = None, stream=None) -> tuple[int, list]:

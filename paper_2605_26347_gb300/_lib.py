@@ -66,6 +66,7 @@ class PlanInfo(C.Structure):
         ("support_table", C.c_int32 * 64),
         ("tile_size", C.c_int32),
         ("truncated", C.c_int32),
+        ("weighted", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -110,6 +111,8 @@ _PROTOS = {
     "rimo_surrogate_fit": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P, _P]),
     "rimo_surrogate_get_w_scale": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rimo_surrogate_set_w_scale": (C.c_int, [_P, C.c_float]),
+    "rimo_plan_set_weights": (C.c_int, [_P, _P, _P]),
+    "rimo_briggs_weights": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

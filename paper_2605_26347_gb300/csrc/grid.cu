@@ -580,6 +580,7 @@ struct BuildArgs {
     int L, hmax, J, literal;
     int64_t v0, nvis;        // sorted visibilities [v0, v0 + nvis)
     uint32_t* fx;
+    const float* wt;         // data weights (sorted order) multiplying the tiles, or null
 };
 
 __device__ __forceinline__ float kb_eval(float t, float invhalf, const float* coef, int nterm) {
@@ -768,9 +769,10 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
             Ab[su * 19 + b] = make_float2(ar, ai);
         }
         __syncwarp();
-        // 3b. T[a][b] = sum_su w_u[a - su] A[su][b]
+        // 3b. T[a][b] = sum_su w_u[a - su] A[su][b], times the data weight
         float2* G = A.gblk[mt.pos >> 24] + mt.off;
         const int n = S * S;
+        const float wk = A.wt ? A.wt[k] : 1.f;
         for (int e = lane; e < n + (n & 1); e += 32) {
             float2 out = make_float2(0.f, 0.f);
             if (e < n) {
@@ -784,6 +786,8 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
                     }
                 }
             }
+            out.x *= wk;
+            out.y *= wk;
             G[e] = out;
             const float m = fabsf(out.x) + fabsf(out.y);
             tmax = fmaxf(tmax, m);
@@ -831,6 +835,7 @@ void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t
     A.v0 = v0;
     A.nvis = n;
     A.fx = p->d_fx;
+    A.wt = p->d_wt;
     const size_t sm = gbuild_smem(p->L, p->hmax);
     void (*kern)(BuildArgs) = p->L == 16 ? gbuild_kernel<16> : p->L == 32 ? gbuild_kernel<32>
                             : p->L == 64 ? gbuild_kernel<64> : gbuild_kernel<128>;

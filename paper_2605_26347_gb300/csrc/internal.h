@@ -134,6 +134,8 @@ struct rimo_plan {
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
     std::vector<std::vector<uint16_t>> trows;  // per bin: uv-tile rows (tu) holding a needed tile
+    float* d_wt = nullptr;      // data weights in sorted order (null: no weighting)
+    float* d_wt_buf = nullptr;  // their buffer (kept when the weighting is removed)
 
     // kernel surrogate (mode RIMO_MODE_SURROGATE) or exact on-the-fly tiles (mode
     // RIMO_MODE_ONTHEFLY): tiles generated per bin at apply time

@@ -566,6 +566,7 @@ struct GenArgs {
     const bf16* W3g;   // [480][128]
     uint32_t* fx;
     int* status;
+    const float* wt;   // data weights (sorted order) multiplying the tiles, or null
 };
 
 __device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
@@ -584,6 +585,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
     float* sb3 = sb2 + 128;
     float* sx = sb3 + GEN_N3;
     int64_t* soff = reinterpret_cast<int64_t*>(sx + 384);
+    __shared__ float swt[128];  // data weight of each row
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
     bool ok = true;
     const int ntile = (A.n + 127) / 128;
     // the next tile's inputs are loaded (raw) while this tile computes
-    float in_u = 0.f, in_v = 0.f, in_w = 0.f;
+    float in_u = 0.f, in_v = 0.f, in_w = 0.f, in_wt = 1.f;
     int64_t in_off = 0;
     auto load_inputs = [&](int t) {
         if (tid < 128 && t < ntile) {
@@ -632,6 +634,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
             in_v = __ldg(A.phiv + k);
             in_w = __ldg(A.wr + k);
             in_off = A.meta[k].off;
+            in_wt = A.wt ? __ldg(A.wt + k) : 1.f;
         }
     };
     load_inputs(blockIdx.x);
@@ -642,6 +645,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
             sx[3 * tid + 1] = 2.f * in_v - 1.f;
             sx[3 * tid + 2] = in_w * A.inv_w;
             soff[tid] = in_off;
+            swt[tid] = in_wt;
         }
         load_inputs(tile + gridDim.x);
         __syncthreads();
@@ -725,6 +729,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
             const int r = 32 * (warp & 3) + lane;
             const bool valid = base + r < A.n;
             float2* dst = A.taps + soff[r];
+            const float wk = swt[r];
             float tmax = 0.f, tsum = 0.f;
 #pragma unroll 1
             for (int c = warp >> 2; c < (SUR_TAPS + 15) / 16; c += 2) {
@@ -744,8 +749,9 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
                 for (int i = 0; i < 16; i += 2) {
                     const int q = q0 + i;
                     if (q > SUR_TAPS) break;  // q = 224, 225: the last tap and the pad
-                    float2 t0 = make_float2(re[i] + sb3[q], im[i] + sb3[GEN_IM + q]);
-                    float2 t1 = q + 1 < SUR_TAPS ? make_float2(re[i + 1] + sb3[q + 1], im[i + 1] + sb3[GEN_IM + q + 1])
+                    float2 t0 = make_float2(wk * (re[i] + sb3[q]), wk * (im[i] + sb3[GEN_IM + q]));
+                    float2 t1 = q + 1 < SUR_TAPS ? make_float2(wk * (re[i + 1] + sb3[q + 1]),
+                                                               wk * (im[i + 1] + sb3[GEN_IM + q + 1]))
                                                  : make_float2(0.f, 0.f);
                     const float m0 = fabsf(t0.x) + fabsf(t0.y), m1 = fabsf(t1.x) + fabsf(t1.y);
                     tmax = fmaxf(tmax, fmaxf(m0, m1));
@@ -799,6 +805,7 @@ int surrogate_generate(rimo_plan* p, int bin, cudaStream_t s) {
     A.W3g = sur->W3g;
     A.fx = p->d_fx;
     A.status = p->d_status;
+    A.wt = p->d_wt;
     RIMO_CUDA(cudaFuncSetAttribute(sur_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEN_SMEM));
     const int64_t ntile = (n + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntile, (int64_t)p->n_sm);
@@ -965,6 +972,7 @@ rimo_status rimo_surrogate_fit(rimo_surrogate_t s, rimo_plan_t exact, int64_t n_
     if (!s || !exact) fail(RIMO_ERR_INVALID_ARG, "null argument");
     if (exact->mode == RIMO_MODE_SURROGATE || exact->d_gblocks.empty())
         fail(RIMO_ERR_INVALID_ARG, "training needs a plan with stored exact tiles");
+    if (exact->d_wt) fail(RIMO_ERR_STATE, "training needs unweighted tiles (remove the plan's weighting first)");
     if (exact->J + exact->prm.max_wsupport - 1 != SUR_S)
         fail(RIMO_ERR_INVALID_ARG, "training tiles must be 15 x 15 (kb_support + max_wsupport - 1 = 15)");
     if (n_samples <= 0 || steps <= 0 || !(lr > 0.f)) fail(RIMO_ERR_INVALID_ARG, "n_samples, steps, lr must be > 0");

@@ -86,3 +86,21 @@ def test_planner_budget_regimes_match_oracle():
         est = pkg.estimate(uvw, _params(pkg, 256, fov, mem_budget_bytes=budget))
         r = opl.choose(uvw, opl.PlanParams(nx=256, ny=256, fov_x=fov, fov_y=fov, mem_budget_bytes=budget))
         assert (est["P"], est["mode"]) == (r["P"], r["mode"]), budget
+
+
+def test_briggs_weights_match_oracle_on_the_host():
+    # host logic of the library (no GPU): Briggs' robust weights against the oracle's
+    import paper_2605_26347_gb300 as pkg
+    from oracle import weighting
+    uvw = synth.make_uvw(20000, 60, 1.28e9, 9)
+    fov = math.radians(1.5)
+    for R in (-2.0, 0.0, 0.5, 2.0):
+        got = pkg.briggs_weights(uvw, 128, 96, fov, 0.8 * fov, R)
+        want = weighting.briggs_weights(uvw, 128, 96, fov, 0.8 * fov, R)
+        assert np.max(np.abs(got - want) / want) < 1e-6, R
+    with pytest.raises(pkg.RimoError):
+        pkg.briggs_weights(uvw, 0, 96, fov, fov, 0.0)
+    bad = uvw.copy()
+    bad[3, 0] = np.nan
+    with pytest.raises(pkg.RimoError):
+        pkg.briggs_weights(bad, 128, 96, fov, fov, 0.0)
