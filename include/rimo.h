@@ -422,6 +422,25 @@ rimo_status rimo_briggs_weights(const double* uvw, int64_t M, int32_t nx, int32_
                                 double fov_y, double robust, float* w_out);
 
 /*
+ * One forward-backward update of Eq. 4 with the denoising step D = projection onto the
+ * non-negative real images (the image model of Eq. 3): out = max(Re x + gamma (Re dirty -
+ * Re g), 0) + 0i elementwise, where g = Phi^dagger Phi x (an apply's output) and dirty =
+ * Phi^dagger y.  x, g, dirty, out: device, n complex values (out may alias x).
+ * Enqueued on `stream`.  Errors: INVALID_ARG (null pointer, n < 0, gamma < 0 or not finite).
+ */
+rimo_status rimo_fb_step(const rimo_cfloat* x, const rimo_cfloat* g, const rimo_cfloat* dirty, float gamma,
+                         rimo_cfloat* out, int64_t n, void* stream);
+
+/*
+ * *result = Re sum_i conj(a_i) b_i over n complex values (device buffers), accumulated in
+ * FP64 in a fixed order (deterministic); for the data fidelity 1/2 ||Phi x - y||^2 =
+ * 1/2 (<x, Phi^dagger Phi x> - 2 <x, Phi^dagger y> + ||y||^2) and power iterations.
+ * result: host.  Synchronises `stream`; concurrent calls take turns.
+ * Errors: INVALID_ARG (null pointer, n < 0), CUDA.
+ */
+rimo_status rimo_image_dot(const rimo_cfloat* a, const rimo_cfloat* b, int64_t n, double* result, void* stream);
+
+/*
  * Kernel surrogate as the plan's tile generator.  A plan created with mode
  * RIMO_MODE_SURROGATE (kb_support + max_wsupport - 1 must be 15) places every visibility
  * with the largest support (15 x 15 tiles), keeps one Fourier block per w-bin and stores

@@ -340,6 +340,33 @@ class Batch:
         return {"n_plans": n.value, "captures": caps.value}
 
 
+def fb_step(x, g, dirty, gamma: float, out=None, stream=None):
+    """rimo_fb_step: Eq. 4 with the projection onto non-negative real images as D
+    (x, g = Phi^dagger Phi x, dirty: complex64 CUDA tensors of one shape)."""
+    torch = _torch()
+    for t, name in ((x, "x"), (g, "g"), (dirty, "dirty")):
+        if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous() and t.shape == x.shape):
+            raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor shaped like x")
+    if out is None:
+        out = torch.empty_like(x)
+    lib = _lib.load()
+    _lib.check(lib.rimo_fb_step(x.data_ptr(), g.data_ptr(), dirty.data_ptr(), float(gamma), out.data_ptr(),
+                                x.numel(), _stream_ptr(stream)))
+    return out
+
+
+def image_dot(a, b, stream=None) -> float:
+    """rimo_image_dot: Re <a, b> of two complex64 CUDA tensors, FP64 accumulation."""
+    torch = _torch()
+    if not (a.is_cuda and b.is_cuda and a.dtype == torch.complex64 and b.dtype == torch.complex64
+            and a.is_contiguous() and b.is_contiguous() and a.numel() == b.numel()):
+        raise ValueError("a and b must be contiguous complex64 CUDA tensors of one size")
+    lib = _lib.load()
+    r = C.c_double()
+    _lib.check(lib.rimo_image_dot(a.data_ptr(), b.data_ptr(), a.numel(), C.byref(r), _stream_ptr(stream)))
+    return r.value
+
+
 def briggs_weights(uvw, nx: int, ny: int, fov_x: float, fov_y: float, robust: float) -> np.ndarray:
     """rimo_briggs_weights: Briggs' robust weights (float32, caller order)."""
     lib = _lib.load()

@@ -113,6 +113,8 @@ _PROTOS = {
     "rimo_surrogate_set_w_scale": (C.c_int, [_P, C.c_float]),
     "rimo_plan_set_weights": (C.c_int, [_P, _P, _P]),
     "rimo_briggs_weights": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P]),
+    "rimo_fb_step": (C.c_int, [_P, _P, _P, C.c_float, _P, C.c_int64, _P]),
+    "rimo_image_dot": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_double), _P]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }
