@@ -81,7 +81,8 @@ typedef enum rimo_n_weight {
  *                     (Section 3.1); in (0, 1], default 0.9999.
  *   mem_budget_bytes  device memory budget m* for the stored matrices (0 = no limit).
  *   n_wbins           number P of w-bins (0 = chosen by the cost model, Eq. 10).
- *   n_blocks          Fourier blocks per plan (0 = by block_bytes_max).
+ *   n_blocks          Fourier blocks of G: byte limit total / n_blocks (0 = by block_bytes_max);
+ *                     blocks do not span w-bins, so a plan holds n_blocks .. n_blocks + P.
  *   mode              rimo_mode.
  *   n_weight          rimo_n_weight.
  *   plan_fraction     fraction of the data used for planning (default 0.01).
