@@ -538,6 +538,8 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // Layer 3's rows are packed so that real and imaginary outputs start at 16-aligned TMEM
 // columns: rows [0, 225) the real parts, [240, 465) the imaginary parts, the rest zero.
 constexpr int GEN_THREADS = 256;
+constexpr int GEN_WG = GEN_THREADS / 128;  // warp groups: each covers the 128 TMEM lanes once
+constexpr int GEN_HW = MLP_H / GEN_WG;      // hidden units (columns) per warp group
 constexpr int GEN_N3 = 480, GEN_IM = 240;
 constexpr size_t GEN_SW2 = (size_t)MLP_H * MLP_H * 2, GEN_SW3 = (size_t)GEN_N3 * MLP_H * 2, GEN_SA = 128 * MLP_H * 2;
 constexpr size_t GEN_SMEM = GEN_SW2 + GEN_SW3 + GEN_SA + (384 + 128 + 128 + GEN_N3 + 384) * 4 + 128 * 8;
@@ -586,6 +588,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
     float* sx = sb3 + GEN_N3;
     int64_t* soff = reinterpret_cast<int64_t*>(sx + 384);
     __shared__ float swt[128];  // data weight of each row
+    __shared__ float s_tsum[GEN_WG][128];  // per warp group: partial tap sums of each row
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -649,23 +652,24 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
         }
         load_inputs(tile + gridDim.x);
         __syncthreads();
-        {   // layer 1: row r, hidden units [64 h, 64 h + 64)
+        {   // layer 1: row r, hidden units [GEN_HW h, GEN_HW (h + 1))
             const int r = tid & 127, h = tid >> 7;
             const float x0 = sx[3 * r], x1 = sx[3 * r + 1], x2 = sx[3 * r + 2];
 #pragma unroll 1
-            for (int g = 0; g < 8; ++g) {
+            for (int g = 0; g < GEN_HW / 8; ++g) {
                 uint32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float z[2];
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const int j = 64 * h + 8 * g + 2 * q + u;
+                        const int j = GEN_HW * h + 8 * g + 2 * q + u;
                         z[u] = gelu_f(fmaf(x0, sW1[3 * j], fmaf(x1, sW1[3 * j + 1], fmaf(x2, sW1[3 * j + 2], sb1[j]))));
                     }
                     w[q] = pack_bf2(z[0], z[1]);
                 }
-                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, 64 * h + 8 * g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r, GEN_HW * h + 8 * g, 128)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         tc::fence_proxy_async();
@@ -683,11 +687,11 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
         phase ^= 1;
         if (__syncthreads_or(!ok)) break;
         tc::fence_after_sync();
-        {   // layer-2 read-out: row 32 (warp % 4) + lane, columns [64 (warp / 4), + 64)
+        {   // layer-2 read-out: row 32 (warp % 4) + lane, columns [GEN_HW (warp / 4), + GEN_HW)
             const int r = 32 * (warp & 3) + lane;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 32) {  // two 16-column loads in flight per wait
-                const int col = 64 * (warp >> 2) + c0;
+            for (int c0 = 0; c0 < GEN_HW; c0 += 32) {  // two 16-column loads in flight per wait
+                const int col = GEN_HW * (warp >> 2) + c0;
                 uint32_t va[16], vb[16];
                 tc::tmem_ld16_async(tmem + lane_base + (uint32_t)col, va);
                 tc::tmem_ld16_async(tmem + lane_base + (uint32_t)(col + 16), vb);
@@ -725,50 +729,62 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
         phase ^= 1;
         if (__syncthreads_or(!ok)) break;
         tc::fence_after_sync();
-        {   // layer-3 read-out: chunks of 16 taps; warps 0-3 the even chunks, 4-7 the odd ones
+        {   // layer-3 read-out: chunks of 16 taps (warp groups take every GEN_WG-th chunk).  The
+            // chunk's 32 rows pass through a warp-private 4 KB of the A buffer (free once the
+            // layer-3 MMAs completed) so that the warp writes 128-byte row segments, not
+            // scattered 16-byte pieces; pieces are XOR-swizzled by row against bank conflicts.
             const int r = 32 * (warp & 3) + lane;
             const bool valid = base + r < A.n;
-            float2* dst = A.taps + soff[r];
             const float wk = swt[r];
+            float4* stage = reinterpret_cast<float4*>(sA) + warp * 256;  // [32 rows][8 pieces]
             float tmax = 0.f, tsum = 0.f;
 #pragma unroll 1
-            for (int c = warp >> 2; c < (SUR_TAPS + 15) / 16; c += 2) {
+            for (int c = warp >> 2; c < (SUR_TAPS + 15) / 16; c += GEN_WG) {
                 const int q0 = 16 * c;
                 uint32_t rr[16], ri[16];
                 tc::tmem_ld16_async(tmem + lane_base + (uint32_t)q0, rr);
                 tc::tmem_ld16_async(tmem + lane_base + (uint32_t)(GEN_IM + q0), ri);
                 tc::tmem_wait_ld_tied(rr);
                 tc::reg_tie(ri);
-                float re[16], im[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    re[i] = __uint_as_float(rr[i]);
-                    im[i] = __uint_as_float(ri[i]);
-                }
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const int q = q0 + i;
-                    if (q > SUR_TAPS) break;  // q = 224, 225: the last tap and the pad
-                    float2 t0 = make_float2(wk * (re[i] + sb3[q]), wk * (im[i] + sb3[GEN_IM + q]));
-                    float2 t1 = q + 1 < SUR_TAPS ? make_float2(wk * (re[i + 1] + sb3[q + 1]),
-                                                               wk * (im[i + 1] + sb3[GEN_IM + q + 1]))
-                                                 : make_float2(0.f, 0.f);
+                for (int j = 0; j < 8; ++j) {  // piece j: taps q0 + 2j, q0 + 2j + 1 (zero past the tile)
+                    const int q = q0 + 2 * j;
+                    const float2 t0 = q < SUR_TAPS ? make_float2(wk * (__uint_as_float(rr[2 * j]) + sb3[q]),
+                                                                 wk * (__uint_as_float(ri[2 * j]) + sb3[GEN_IM + q]))
+                                                   : make_float2(0.f, 0.f);
+                    const float2 t1 = q + 1 < SUR_TAPS
+                                          ? make_float2(wk * (__uint_as_float(rr[2 * j + 1]) + sb3[q + 1]),
+                                                        wk * (__uint_as_float(ri[2 * j + 1]) + sb3[GEN_IM + q + 1]))
+                                          : make_float2(0.f, 0.f);
                     const float m0 = fabsf(t0.x) + fabsf(t0.y), m1 = fabsf(t1.x) + fabsf(t1.y);
                     tmax = fmaxf(tmax, fmaxf(m0, m1));
                     tsum += m0 + m1;
-                    if (valid) *reinterpret_cast<float4*>(dst + q) = make_float4(t0.x, t0.y, t1.x, t1.y);
+                    stage[lane * 8 + (j ^ (lane & 7))] = make_float4(t0.x, t0.y, t1.x, t1.y);
                 }
+                __syncwarp();
+                // a tile holds 226 taps (225 and the pad): the last chunk has one piece
+                const int npc = q0 + 16 <= SUR_TAPS + 1 ? 8 : (SUR_TAPS + 1 - q0) / 2;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int row = 4 * it + (lane >> 3), pc = lane & 7;
+                    const int rg = 32 * (warp & 3) + row;
+                    if (pc < npc && base + rg < A.n)
+                        *reinterpret_cast<float4*>(A.taps + soff[rg] + q0 + 2 * pc) = stage[row * 8 + (pc ^ (row & 7))];
+                }
+                __syncwarp();
             }
-            if (valid) {
-                // each warp group sees half the taps of a row: the row's tap sum is at most
-                // twice the larger half
-                atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
-                atomicMax(A.fx + FX_T1, __float_as_uint(2.f * tsum));
-            }
+            if (valid) atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
+            s_tsum[warp >> 2][r] = valid ? tsum : 0.f;  // each warp group holds a share of the row
         }
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        if (tid < 128 && base + tid < A.n) {
+            float t = 0.f;
+#pragma unroll
+            for (int q = 0; q < GEN_WG; ++q) t += s_tsum[q][tid];
+            atomicMax(A.fx + FX_T1, __float_as_uint(t));
+        }
     }
     if (!ok && tid == 0) atomicExch(A.status, 2);
     tc::fence_before_sync();
