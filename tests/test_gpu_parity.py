@@ -108,6 +108,9 @@ def test_mono256_fused_equals_sequential_and_adjoint_identity(mono256):
          kw=dict(n_wbins=2, kb_support=9, max_wsupport=5, taper_literal=1, wkernel_L=32, tile_size=32)),
     # automatic P, J = 3, energy fraction 0.99, tile size 64
     dict(nx=128, ny=128, fx=3.0, fy=3.0, m=5000, kw=dict(kb_support=3, w_norm_frac=0.99, tile_size=64)),
+    # the largest tiles: J = 11 with 9 x 9 w-kernels, S = 19 (two column groups per tap row,
+    # taps re-read for the grid step)
+    dict(nx=128, ny=128, fx=2.0, fy=2.0, m=2500, kw=dict(n_wbins=2, kb_support=11, max_wsupport=9, w_norm_frac=1.0)),
     # w-kernel grids L = 16 (4 lanes per folded column) and L = 128 (2 columns per lane)
     dict(nx=128, ny=128, fx=2.0, fy=2.0, m=1500, kw=dict(n_wbins=2, max_wsupport=3, wkernel_L=16)),
     dict(nx=128, ny=128, fx=2.5, fy=2.5, m=1500, kw=dict(n_wbins=2, wkernel_L=128)),

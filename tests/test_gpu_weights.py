@@ -68,6 +68,17 @@ def test_unit_weights_are_exactly_unweighted(case):
         plan.set_weights(None)
 
 
+def test_zero_weights_give_the_zero_operator(case):
+    w, plan, _, _, _ = case
+    plan.set_weights(np.zeros(w.uvw.shape[0], np.float32))
+    try:
+        x = to_dev(w.sky)
+        assert not np.any(to_host(plan.phi_adj_phi(x)))
+        assert not np.any(to_host(plan.phi(x)))
+    finally:
+        plan.set_weights(None)
+
+
 def test_generated_tiles_and_holographic_matrix_take_the_weights(case):
     import paper_2605_26347_gb300 as pkg
     w, plan, _, opw, wt = case
