@@ -145,10 +145,27 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
     for (int q = 0; q < Q; ++q) {
         if (NS > 1) {
             const int jm = (t + q * T) & (NS - 1);
+            if constexpr (R == 16) {
+                // W^r for r = 1 .. 15 from two table entries (W and W^4), at most three
+                // products deep: two loads instead of fifteen
+                float2 w[16];
+                w[1] = __ldg(&tws[NS + jm]);
+                w[4] = __ldg(&tws[4 * NS + jm]);
+                w[2] = cmul(w[1], w[1]);
+                w[3] = cmul(w[2], w[1]);
+                w[8] = cmul(w[4], w[4]);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tws[r * NS + jm]);
-                v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+                for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+#pragma unroll
+                for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+                for (int r = 1; r < 16; ++r) v[q * R + r] = INV ? cmulc(v[q * R + r], w[r]) : cmul(v[q * R + r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tws[r * NS + jm]);
+                    v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+                }
             }
         }
         dft_r<R, INV>(&v[q * R]);
