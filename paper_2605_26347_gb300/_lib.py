@@ -41,6 +41,7 @@ class PlanParams(C.Structure):
         ("wkernel_L", C.c_int32),
         ("tile_size", C.c_int32),
         ("block_bytes_max", C.c_int64),
+        ("wkernel_table", C.c_int32),
     ]
 
 

@@ -134,6 +134,9 @@ struct rimo_plan {
     int device = 0;                // CUDA device the plan lives on
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
     std::vector<std::vector<uint16_t>> trows;  // per bin: uv-tile rows (tu) holding a needed tile
+    float2* d_kwtab = nullptr;  // tabulated folded w-kernels (wkernel_table > 0), (kw_n + 3) x 25
+    int kw_n = 0;
+    double kw_w0 = 0.0, kw_dw = 0.0;  // sample j at w = kw_w0 + j kw_dw
     float* d_wt = nullptr;      // data weights in sorted order (null: no weighting)
     float* d_wt_buf = nullptr;  // their buffer (kept when the weighting is removed)
 
@@ -230,6 +233,7 @@ void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
 // exact tiles of the sorted visibilities [v0, v0 + n) into their block (the on-the-fly mode's
 // scratch), with the tap bounds of the fixed-point grid step
+void launch_kwtab(const rimo_plan* p, cudaStream_t s);
 void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t s);
 
 // The three applies on stream s (defined in apply.cu).

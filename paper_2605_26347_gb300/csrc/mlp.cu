@@ -625,6 +625,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
     uint32_t phase = 0;
     bool ok = true;
+    float run_tmax = 0.f, run_t1 = 0.f;  // running bounds over this thread's tiles
     const int ntile = (A.n + 127) / 128;
     // the next tile's inputs are loaded (raw) while this tile computes
     float in_u = 0.f, in_v = 0.f, in_w = 0.f, in_wt = 1.f;
@@ -773,7 +774,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
                 }
                 __syncwarp();
             }
-            if (valid) atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
+            if (valid) run_tmax = fmaxf(run_tmax, tmax);
             s_tsum[warp >> 2][r] = valid ? tsum : 0.f;  // each warp group holds a share of the row
         }
         tc::fence_before_sync();
@@ -783,8 +784,18 @@ __global__ void __launch_bounds__(GEN_THREADS, 1) sur_gen_kernel(GenArgs A) {
             float t = 0.f;
 #pragma unroll
             for (int q = 0; q < GEN_WG; ++q) t += s_tsum[q][tid];
-            atomicMax(A.fx + FX_T1, __float_as_uint(t));
+            run_t1 = fmaxf(run_t1, t);
         }
+    }
+    // the bounds: one atomic per warp for the whole launch (not one per visibility)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        run_tmax = fmaxf(run_tmax, __shfl_xor_sync(0xffffffffu, run_tmax, o));
+        run_t1 = fmaxf(run_t1, __shfl_xor_sync(0xffffffffu, run_t1, o));
+    }
+    if (lane == 0) {
+        atomicMax(A.fx + FX_TMAX, __float_as_uint(run_tmax));
+        atomicMax(A.fx + FX_T1, __float_as_uint(run_t1));
     }
     if (!ok && tid == 0) atomicExch(A.status, 2);
     tc::fence_before_sync();

@@ -90,6 +90,8 @@ static void validate(const rimo_plan_params& q) {
     if (q.wkernel_L != 0 && (!is_pow2(q.wkernel_L) || q.wkernel_L < 16 || q.wkernel_L > 128))
         bad("wkernel_L must be 0 or a power of two in [16, 128]");
     if (q.tile_size != 0 && q.tile_size != 32 && q.tile_size != 64) bad("tile_size must be 0, 32 or 64");
+    if (q.wkernel_table != 0 && (q.wkernel_table < 16 || q.wkernel_table > (1 << 22)))
+        bad("wkernel_table must be 0 or in [16, 2^22]");
     if (q.kb_beta < 0) bad("kb_beta must be >= 0");
 }
 
@@ -477,6 +479,14 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
 
     // ---- device
     build_tables(p, s);
+    if (q.wkernel_table > 0) {
+        // folded kernels sampled over [-max|w_r|, max|w_r|] (one sample of margin each side)
+        p->kw_n = q.wkernel_table;
+        p->kw_dw = 2.0 * wr_max / p->kw_n;
+        p->kw_w0 = -wr_max - p->kw_dw;
+        p->d_kwtab = (float2*)dev_alloc(p, (size_t)(p->kw_n + 3) * 25 * sizeof(float2));
+        launch_kwtab(p, s);
+    }
     p->d_meta = upload(p, meta, s);
     // chunk descriptors: GTG_CHUNK consecutive visibilities of a unit share one tap range
     {
