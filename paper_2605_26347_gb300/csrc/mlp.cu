@@ -26,7 +26,19 @@ namespace rimo {
 
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// erf by the rational approximation of Abramowitz & Stegun (1964), eq. 7.1.26:
+// erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2}, t = 1 / (1 + p x), x >= 0,
+// |error| <= 1.5e-7 (odd extension to x < 0); one reciprocal and one exponential.
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    return copysignf(fmaf(-poly, __expf(-ax * ax), 1.f), x);
+}
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 (the network's activation everywhere it
+// runs forward: training, batched forward, tile generation)
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }

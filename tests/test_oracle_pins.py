@@ -374,3 +374,21 @@ def test_automatic_bins_avoid_truncated_kernels():
                 assert d["truncated"]
     else:
         assert ch["P"] == max(by_p)
+
+
+def test_rational_erf_meets_its_published_bound():
+    # the network's GELU on the device uses Abramowitz & Stegun eq. 7.1.26 for erf; its
+    # error bound (1.5e-7) checked against SciPy's erf in FP64 and with FP32 arithmetic
+    x = np.linspace(-6.0, 6.0, 200001)
+
+    def erf_as(x, dt):
+        x = x.astype(dt)
+        ax = np.abs(x)
+        t = dt(1.0) / (dt(0.3275911) * ax + dt(1.0))
+        poly = t * (dt(0.254829592) + t * (dt(-0.284496736) + t * (dt(1.421413741) + t * (dt(-1.453152027)
+                                                                                          + t * dt(1.061405429)))))
+        return np.copysign(dt(1.0) - poly * np.exp(-ax * ax), x)
+
+    assert np.max(np.abs(erf_as(x, np.float64) - ss.erf(x))) < 1.5e-7
+    # FP32 rounding of 1 - poly e near 1 adds a few units of 6e-8
+    assert np.max(np.abs(erf_as(x, np.float32).astype(np.float64) - ss.erf(x))) < 1e-6
