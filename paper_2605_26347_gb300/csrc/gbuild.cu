@@ -239,57 +239,54 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) kwtab_kernel(BuildArgs A) {
 // 3a. A[su][b] = sum_sv K(su - h, sv - h) w_v[b - sv]   (su < S_w, b < S)
 // 3b. T[a][b]  = sum_su w_u[a - su] A[su][b]            (a, b < S), times the weight wk,
 // stored to G (and the pad entry of an odd count), with the running tap bounds.
+// Lane b < S owns column b: its S_w values of A stay in registers, the folded kernel is
+// read by broadcast, and with S_w and J known every tap condition resolves at compile time.
 template <int J, int SW>
-__device__ __forceinline__ void conv_tile(const float2* Kq, const float* taps, float2* Ab, float2* G, float wk,
-                                          int lane, float& tmax, float& tsum) {
-    constexpr int S = SW + J - 1, h = SW / 2, N = S * S, NP = N + (N & 1);
-#pragma unroll 1
-    for (int e0 = 0; e0 < SW * S; e0 += 32) {
-        const int e = e0 + lane;
-        if (e < SW * S) {
-            const int su = e / S, b = e - su * S;
-            const float2* Kr = Kq + abs(su - h) * BUILD_TQ;
+__device__ __forceinline__ void conv_tile(const float2* Kq, const float* taps, float2* G, float wk, int lane,
+                                          float& tmax, float& tsum) {
+    constexpr int S = SW + J - 1, h = SW / 2, N = S * S;
+    if (lane < S) {
+        const int b = lane;
+        float wvb[SW];  // w_v[b - sv], zero outside [0, J)
+#pragma unroll
+        for (int sv = 0; sv < SW; ++sv) {
+            const int i = b - sv;
+            wvb[sv] = (i >= 0 && i < J) ? taps[16 + (i >= 0 && i < J ? i : 0)] : 0.f;
+        }
+        float2 acol[SW];
+#pragma unroll
+        for (int su = 0; su < SW; ++su) {
             float ar = 0.f, ai = 0.f;
 #pragma unroll
             for (int sv = 0; sv < SW; ++sv) {
-                const int i = b - sv;
-                if (i >= 0 && i < J) {
-                    const float wv = taps[16 + i];
-                    const float2 kv = Kr[abs(sv - h)];
-                    ar = fmaf(kv.x, wv, ar);
-                    ai = fmaf(kv.y, wv, ai);
-                }
+                const float2 kv = Kq[(su > h ? su - h : h - su) * BUILD_TQ + (sv > h ? sv - h : h - sv)];
+                ar = fmaf(kv.x, wvb[sv], ar);
+                ai = fmaf(kv.y, wvb[sv], ai);
             }
-            Ab[su * 19 + b] = make_float2(ar, ai);
+            acol[su] = make_float2(ar, ai);
         }
-    }
-    __syncwarp();
-#pragma unroll 1
-    for (int e0 = 0; e0 < NP; e0 += 32) {
-        const int e = e0 + lane;
-        if (e < NP) {
-            float2 out = make_float2(0.f, 0.f);
-            if (e < N) {
-                const int a = e / S, b = e - a * S;
+        float wu[J];
 #pragma unroll
-                for (int su = 0; su < SW; ++su) {
-                    const int i = a - su;
-                    if (i >= 0 && i < J) {
-                        const float wu = taps[i];
-                        const float2 av = Ab[su * 19 + b];
-                        out.x = fmaf(wu, av.x, out.x);
-                        out.y = fmaf(wu, av.y, out.y);
-                    }
+        for (int i = 0; i < J; ++i) wu[i] = taps[i];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            float2 out = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int su = 0; su < SW; ++su) {
+                if (a - su >= 0 && a - su < J) {
+                    out.x = fmaf(wu[a - su], acol[su].x, out.x);
+                    out.y = fmaf(wu[a - su], acol[su].y, out.y);
                 }
             }
             out.x *= wk;
             out.y *= wk;
-            G[e] = out;
+            G[a * S + b] = out;
             const float m = fabsf(out.x) + fabsf(out.y);
             tmax = fmaxf(tmax, m);
             tsum += m;
         }
     }
+    if ((N & 1) && lane == 0) G[N] = make_float2(0.f, 0.f);  // the even-count pad
 }
 
 // the same for any J and S_w (sizes at run time)
@@ -394,11 +391,11 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
         bool done = false;
         if (A.J == 7) {  // the common support: sizes known at compile time
             switch (Sw) {
-                case 1: conv_tile<7, 1>(Kq, taps, Ab, G, wk, lane, tmax, tsum); done = true; break;
-                case 3: conv_tile<7, 3>(Kq, taps, Ab, G, wk, lane, tmax, tsum); done = true; break;
-                case 5: conv_tile<7, 5>(Kq, taps, Ab, G, wk, lane, tmax, tsum); done = true; break;
-                case 7: conv_tile<7, 7>(Kq, taps, Ab, G, wk, lane, tmax, tsum); done = true; break;
-                case 9: conv_tile<7, 9>(Kq, taps, Ab, G, wk, lane, tmax, tsum); done = true; break;
+                case 1: conv_tile<7, 1>(Kq, taps, G, wk, lane, tmax, tsum); done = true; break;
+                case 3: conv_tile<7, 3>(Kq, taps, G, wk, lane, tmax, tsum); done = true; break;
+                case 5: conv_tile<7, 5>(Kq, taps, G, wk, lane, tmax, tsum); done = true; break;
+                case 7: conv_tile<7, 7>(Kq, taps, G, wk, lane, tmax, tsum); done = true; break;
+                case 9: conv_tile<7, 9>(Kq, taps, G, wk, lane, tmax, tsum); done = true; break;
                 default: break;
             }
         }
