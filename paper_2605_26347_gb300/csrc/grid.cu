@@ -234,7 +234,7 @@ __device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float
 }
 
 // Warp-specialised pipeline per block:
-//   producer warp : for each chunk (16 consecutive visibilities of a unit) streams their
+//   producer warp : for each chunk (GTG_CHUNK consecutive visibilities of a unit) streams their
 //                   16-byte metadata and their taps (one contiguous range, from a chunk
 //                   descriptor) into ring slot b with cp.async.bulk, once the consumers
 //                   released the slot;
@@ -490,7 +490,7 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.shift = p->TS == 64 ? 6 : 5;
     A.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * A.ntv;
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
-    // prefetch the X patches when a double buffer still leaves a 4-deep tap ring
+    // prefetch the X patches when a double buffer still leaves a GTG_NBUF-deep tap ring
     A.prefetch = MODE != 1 && gtg_smem(p, MODE, 4, true) <= limit;
     A.nbuf = GTG_NBUF;
     while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf, A.prefetch) > limit) --A.nbuf;

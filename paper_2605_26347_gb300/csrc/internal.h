@@ -59,7 +59,7 @@ struct TileDesc {
     int64_t cb;   // index of the unit's first chunk descriptor
 };
 
-// One chunk of at most 16 consecutive visibilities of a unit: their taps are the byte
+// One chunk of at most GTG_CHUNK consecutive visibilities of a unit: their taps are the byte
 // range [8 off, 8 off + bytes) of Fourier block `block`.
 struct ChunkDesc {
     int64_t off;
