@@ -42,7 +42,8 @@ def test_invalid_arguments_are_rejected(rimo_lib):
     import paper_2605_26347_gb300 as pkg
     uvw = synth.make_uvw(100, 60, 1.28e9, 3)
     for bad in (dict(nx=100), dict(oversampling=3), dict(kb_support=6), dict(max_wsupport=11),
-                dict(w_norm_frac=0.0), dict(plan_fraction=2.0), dict(tile_size=48)):
+                dict(w_norm_frac=0.0), dict(plan_fraction=2.0), dict(tile_size=48), dict(wkernel_table=8),
+                dict(wkernel_table=-1)):
         p = _params(pkg, 256, math.radians(1.0))
         for k, v in bad.items():
             setattr(p, k, v)
