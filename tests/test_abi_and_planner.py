@@ -105,3 +105,35 @@ def test_briggs_weights_match_oracle_on_the_host():
     bad[3, 0] = np.nan
     with pytest.raises(pkg.RimoError):
         pkg.briggs_weights(bad, 128, 96, fov, fov, 0.0)
+
+
+def test_python_structures_match_the_c_header(tmp_path):
+    # the ctypes views of rimo_plan_params and rimo_plan_info against the header's layout,
+    # compiled by the host C compiler (sizes and every field offset)
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_2605_26347_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rimo.h"', 'int main(void) {']
+    for cname, py in (("rimo_plan_params", _lib.PlanParams), ("rimo_plan_info", _lib.PlanInfo)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = {}
+    for line in out:
+        if line:
+            name, field, val = line.split()
+            want[(name, field)] = int(val)
+    for cname, py in (("rimo_plan_params", _lib.PlanParams), ("rimo_plan_info", _lib.PlanInfo)):
+        assert C.sizeof(py) == want[(cname, "size")], cname
+        for f, _ in py._fields_:
+            assert getattr(py, f).offset == want[(cname, f)], (cname, f)
