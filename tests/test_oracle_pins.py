@@ -392,3 +392,25 @@ def test_rational_erf_meets_its_published_bound():
     assert np.max(np.abs(erf_as(x, np.float64) - ss.erf(x))) < 1.5e-7
     # FP32 rounding of 1 - poly e near 1 adds a few units of 6e-8
     assert np.max(np.abs(erf_as(x, np.float32).astype(np.float64) - ss.erf(x))) < 1e-6
+
+
+def test_cubic_interpolation_of_wkernels_in_w():
+    # The library's optional kernel table rests on K(t; w_r) being smooth in w_r: the cubic
+    # Lagrange interpolant through equispaced samples (8192 intervals over [-w_max, w_max],
+    # as the 4096^2 / 3 deg workload uses) reproduces the oracle's kernels between the samples
+    fov = math.radians(3.0)
+    L, half, w_max, n = 64, 4, 5662.0, 8192
+    dw = 2 * w_max / n
+    rng = np.random.default_rng(12)
+    w = rng.uniform(-w_max, w_max, 40)
+    x = (w + w_max) / dw + 1.0                     # sample j at -w_max + (j - 1) dw
+    j = np.minimum(np.floor(x).astype(int), n)
+    f = x - j
+    nodes = np.stack([-w_max + (j - 2 + i) * dw for i in range(4)], axis=1)     # j - 1 .. j + 2
+    K = wterm.wkernel(nodes.ravel(), L, half, fov, fov).reshape(40, 4, 2 * half + 1, 2 * half + 1)
+    lag = np.stack([-f * (f - 1) * (f - 2) / 6, (f + 1) * (f - 1) * (f - 2) / 2,
+                    -(f + 1) * f * (f - 2) / 2, (f + 1) * f * (f - 1) / 6], axis=1)
+    Ki = np.einsum("qi,qist->qst", lag, K)
+    Ke = wterm.wkernel(w, L, half, fov, fov)
+    err = np.linalg.norm(Ki - Ke, axis=(1, 2)) / np.linalg.norm(Ke, axis=(1, 2))
+    assert err.max() < 1e-7, err.max()
