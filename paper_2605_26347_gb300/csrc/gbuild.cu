@@ -353,6 +353,65 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
     const float invL2 = 1.f / ((float)L * (float)L);
     const float invhalf = 2.f / (float)A.J;
     float tmax = 0.f, t1max = 0.f;
+    if (A.kwtab && A.J == 7) {
+        // tabulated kernels and J = 7: a tile has at most 15 columns, so each half warp takes
+        // one visibility (taps and kernel of half 1 in the otherwise unused row-pass scratch)
+        const int hw = lane >> 4, hl = lane & 15;
+        float2* Kh = hw ? R : Kq;
+        float* th = hw ? reinterpret_cast<float*>(R + BUILD_TQ * BUILD_TQ) : taps;
+        for (int64_t k0 = A.v0 + 2 * ((int64_t)blockIdx.x * BUILD_WARPS + warp); k0 < A.v0 + A.nvis;
+             k0 += 2 * (int64_t)gridDim.x * BUILD_WARPS) {
+            const int64_t k = k0 + hw;
+            const bool act = k < A.v0 + A.nvis;
+            VisMeta mt{};
+            int Sw = 1, h = 0;
+            float w = 0.f;
+            if (act) {
+                mt = A.meta[k];
+                Sw = (int)((mt.pos >> 16) & 255) - 6;
+                h = Sw >> 1;
+                w = A.wr[k];
+                // KB taps: lanes 0 .. 6 along u, 8 .. 14 along v
+                if (hl < 7) th[hl] = kb_eval(A.phiu[k] + 2.5f - (float)hl, invhalf, s_coef, A.kb_nterm);
+                else if (hl >= 8 && hl < 15)
+                    th[16 + hl - 8] = kb_eval(A.phiv[k] + 2.5f - (float)(hl - 8), invhalf, s_coef, A.kb_nterm);
+                // the folded kernel by cubic Lagrange interpolation in w_r
+                const int hq = h + 1;
+                const float x = fminf(fmaxf(fmaf(w, A.tab_inv_dw, A.tab_x0), 1.f), (float)(A.tab_n + 1));
+                const int j = min((int)x, A.tab_n);
+                const float f = x - (float)j;
+                const float l0 = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
+                const float l1 = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
+                const float l2 = -(f + 1.f) * f * (f - 2.f) * 0.5f;
+                const float l3 = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
+                for (int e2 = hl; e2 < hq * hq; e2 += 16) {
+                    const int tx = e2 / hq, ty = e2 - tx * hq, e = tx * BUILD_TQ + ty;
+                    const float2* T = A.kwtab + (size_t)(j - 1) * (BUILD_TQ * BUILD_TQ) + e;
+                    const float2 a0 = __ldg(T), a1 = __ldg(T + 25), a2 = __ldg(T + 50), a3 = __ldg(T + 75);
+                    Kh[e] = make_float2(fmaf(l0, a0.x, fmaf(l1, a1.x, fmaf(l2, a2.x, l3 * a3.x))),
+                                        fmaf(l0, a0.y, fmaf(l1, a1.y, fmaf(l2, a2.y, l3 * a3.y))));
+                }
+            }
+            __syncwarp();
+            float tsum = 0.f;
+            if (act) {
+                float2* G = A.gblk[mt.pos >> 24] + mt.off;
+                const float wk = A.wt ? A.wt[k] : 1.f;
+                switch (Sw) {
+                    case 1: conv_tile<7, 1>(Kh, th, G, wk, hl, tmax, tsum); break;
+                    case 3: conv_tile<7, 3>(Kh, th, G, wk, hl, tmax, tsum); break;
+                    case 5: conv_tile<7, 5>(Kh, th, G, wk, hl, tmax, tsum); break;
+                    case 7: conv_tile<7, 7>(Kh, th, G, wk, hl, tmax, tsum); break;
+                    case 9: conv_tile<7, 9>(Kh, th, G, wk, hl, tmax, tsum); break;
+                    default: break;  // supports are odd and at most 9
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);  // within the half
+            t1max = fmaxf(t1max, tsum);
+            __syncwarp();
+        }
+    } else
     for (int64_t k = A.v0 + (int64_t)blockIdx.x * BUILD_WARPS + warp; k < A.v0 + A.nvis;
          k += (int64_t)gridDim.x * BUILD_WARPS) {
         float tsum = 0.f;
@@ -408,7 +467,10 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
         __syncwarp();
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        t1max = fmaxf(t1max, __shfl_xor_sync(0xffffffffu, t1max, o));  // the two halves' visibilities
+    }
     if (lane == 0) {
         atomicMax(A.fx + FX_TMAX, __float_as_uint(tmax));
         atomicMax(A.fx + FX_T1, __float_as_uint(t1max));
