@@ -159,7 +159,8 @@ void rimo_plan_params_default(rimo_plan_params* p, int32_t nx, int32_t ny, doubl
  * Plan on the host only (Section 3.4, stage 1 of Fig. 3): choose P and the mode from
  * the planning subset without touching a GPU.  uvw: host, M x 3 row-major float64
  * (wavelengths).  Fills *info (per-visibility fields are not computed).
- * Errors: INVALID_ARG.
+ * Errors: INVALID_ARG (also for a NaN or infinite coordinate, or |u| 2 fov_x, |v| 2 fov_y
+ * or |w| of 2^52 or more).
  */
 rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_params* p,
                                rimo_plan_info* info);
@@ -170,7 +171,8 @@ rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_par
  * (Section 3.2), and - in stored-G mode - the de-gridding matrix G on the device.
  * uvw: host, M x 3 row-major float64 (wavelengths); copied, not retained.
  * The plan is built on `stream`; the call synchronises the stream before returning.
- * Errors: INVALID_ARG, OOM, BUDGET (explicit mode beyond the budget), CUDA.
+ * Errors: INVALID_ARG (also for uvw as in rimo_plan_estimate), OOM, BUDGET (explicit mode
+ * beyond the budget), CUDA.
  */
 rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_params* p,
                              void* stream, rimo_plan_t* out);

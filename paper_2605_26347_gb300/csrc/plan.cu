@@ -2,6 +2,7 @@
 // oversampled grid, uv-tile sort, Fourier blocks (Section 3.2) and the device-side
 // build of the de-gridding matrix G.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -93,6 +94,24 @@ static void validate(const rimo_plan_params& q) {
     if (q.wkernel_table != 0 && (q.wkernel_table < 16 || q.wkernel_table > (1 << 22)))
         bad("wkernel_table must be 0 or in [16, 2^22]");
     if (q.kb_beta < 0) bad("kb_beta must be >= 0");
+}
+
+// Every coordinate finite and within the range where the placement (floor, integer
+// conversion, wrap) and the k-means sums stay exact: |u| 2 fov_x, |v| 2 fov_y and |w|
+// below 2^52.  Checked in parallel; the error is raised on the calling thread.
+static void validate_uvw(const double* uvw, int64_t M, const rimo_plan_params& q) {
+    const double lim = 0x1.0p52;
+    std::atomic<bool> bad{false};
+    planner::parallel_for(M, [&](int64_t b, int64_t e) {
+        bool ok = true;
+        for (int64_t k = b; k < e; ++k) {
+            const double u = std::fabs(uvw[3 * k] * (2.0 * q.fov_x)), v = std::fabs(uvw[3 * k + 1] * (2.0 * q.fov_y));
+            const double w = std::fabs(uvw[3 * k + 2]);
+            ok &= (u < lim) & (v < lim) & (w < lim);  // false for NaN as well
+        }
+        if (!ok) bad.store(true);
+    }, 1 << 16);
+    if (bad.load()) fail(RIMO_ERR_INVALID_ARG, "uvw holds a non-finite coordinate or one beyond 2^52 grid cells");
 }
 
 static planner::Params planner_params(const rimo_plan_params& q) {
@@ -632,6 +651,7 @@ rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_par
     try {
         if (!uvw || M <= 0 || !q || !info) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
         validate(*q);
+        validate_uvw(uvw, M, *q);
         planner::Params pr = planner_params(*q);
         planner::Choice ch = planner::choose(uvw, M, pr);
         std::memset(info, 0, sizeof(*info));
@@ -653,6 +673,8 @@ rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_param
     try {
         if (!uvw || M <= 0 || !q || !out) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
         if (M > 2000000000LL) fail(RIMO_ERR_INVALID_ARG, "M above 2e9 visibilities");
+        validate(*q);
+        validate_uvw(uvw, M, *q);
         p = new rimo_plan();
         create_plan(uvw, M, *q, (cudaStream_t)stream, p);
         *out = p;

@@ -51,13 +51,25 @@ std::vector<double> subset_w(const double* uvw, int64_t M, uint64_t seed, double
         for (int64_t k = 0; k < M; ++k) out[k] = uvw[3 * k + 2];
         return out;
     }
-    out.reserve((size_t)(M * frac * 1.1) + 16);
+    // the selection of each index is independent: chunks in parallel, joined in index order
     const uint64_t golden = 0x9E3779B97F4A7C15ull;
-    for (int64_t k = 0; k < M; ++k) {
-        uint64_t st = seed + (uint64_t)(k + 1) * golden;
-        double u = (double)(splitmix64(st) >> 11) * 0x1.0p-53;
-        if (u < frac) out.push_back(uvw[3 * k + 2]);
-    }
+    const int64_t chunk = 1 << 20, nch = (M + chunk - 1) / chunk;
+    std::vector<std::vector<double>> part((size_t)nch);
+    parallel_for(nch, [&](int64_t cb, int64_t ce) {
+        for (int64_t c = cb; c < ce; ++c) {
+            std::vector<double>& o = part[(size_t)c];
+            o.reserve((size_t)(chunk * frac * 1.1) + 16);
+            for (int64_t k = c * chunk; k < std::min(M, (c + 1) * chunk); ++k) {
+                uint64_t st = seed + (uint64_t)(k + 1) * golden;
+                double u = (double)(splitmix64(st) >> 11) * 0x1.0p-53;
+                if (u < frac) o.push_back(uvw[3 * k + 2]);
+            }
+        }
+    }, 1);
+    size_t total = 0;
+    for (const auto& o : part) total += o.size();
+    out.reserve(total);
+    for (const auto& o : part) out.insert(out.end(), o.begin(), o.end());
     return out;
 }
 
@@ -98,15 +110,10 @@ void nearest_all(const double* w, int64_t n, int64_t stride, const std::vector<d
     }, 1 << 14);
 }
 
-std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter) {
-    int64_t n = (int64_t)w.size();
-    std::vector<double> ws(w);
-    std::sort(ws.begin(), ws.end());
-    std::vector<double> c(P);
-    for (int p = 0; p < P; ++p) {
-        int64_t idx = (int64_t)(((p + 0.5) * (double)n) / (double)P);
-        c[p] = ws[std::min<int64_t>(n - 1, idx)];
-    }
+// Lloyd iterations with the labels assigned point by point (any centroid order).
+static void lloyd_points(const std::vector<double>& w, std::vector<double>& c, int max_iter) {
+    const int P = (int)c.size();
+    const int64_t n = (int64_t)w.size();
     std::vector<int32_t> lab(n), nl(n);
     nearest_all(w.data(), n, 1, c, lab.data());
     std::vector<double> sum(P);
@@ -121,8 +128,67 @@ std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter) 
         if (nl == lab) break;
         lab.swap(nl);
     }
+}
+
+// First index of each cluster's run in ascending data: with ascending centroids the nearest
+// centroid (ties to the lower index) is non-decreasing in w, so cluster p holds exactly
+// ws[b[p] .. b[p + 1]).  Returns false when the centroids are not ascending.
+static bool cluster_runs(const std::vector<double>& ws, const std::vector<double>& c,
+                         std::vector<int64_t>& b) {
+    const int P = (int)c.size();
+    const int64_t n = (int64_t)ws.size();
+    if (!std::is_sorted(c.begin(), c.end())) return false;
+    b[0] = 0;
+    b[P] = n;
+    for (int p = 1; p < P; ++p) {
+        int64_t lo = b[p - 1], hi = n;
+        while (lo < hi) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if (nearest_sorted(ws[mid], c.data(), P) < p) lo = mid + 1; else hi = mid;
+        }
+        b[p] = lo;
+    }
+    return true;
+}
+
+std::vector<double> kmeans1d_sorted(const std::vector<double>& ws, int P, int max_iter) {
+    const int64_t n = (int64_t)ws.size();
+    std::vector<double> c(P);
+    for (int p = 0; p < P; ++p) {
+        int64_t idx = (int64_t)(((p + 0.5) * (double)n) / (double)P);
+        c[p] = ws[std::min<int64_t>(n - 1, idx)];
+    }
+    // Each iteration takes the same labels as a point-by-point assignment, so the
+    // iterations and the result are those of Lloyd's algorithm; a cluster's mean is summed
+    // over its run in ascending order.  Centroids stay ascending (each mean lies inside its
+    // own cell); should rounding ever break that, the point-by-point iterations take over.
+    std::vector<int64_t> b(P + 1), nb(P + 1);
+    if (!cluster_runs(ws, c, b)) {
+        lloyd_points(ws, c, max_iter);
+    } else {
+        for (int it = 0; it < max_iter; ++it) {
+            for (int p = 0; p < P; ++p) {
+                if (b[p + 1] == b[p]) continue;  // an empty cluster keeps its centroid
+                double s = 0.0;
+                for (int64_t i = b[p]; i < b[p + 1]; ++i) s += ws[i];
+                c[p] = s / (double)(b[p + 1] - b[p]);
+            }
+            if (!cluster_runs(ws, c, nb)) {
+                lloyd_points(ws, c, max_iter - it - 1);
+                break;
+            }
+            if (nb == b) break;
+            b.swap(nb);
+        }
+    }
     std::sort(c.begin(), c.end());
     return c;
+}
+
+std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter) {
+    std::vector<double> ws(w);
+    std::sort(ws.begin(), ws.end());
+    return kmeans1d_sorted(ws, P, max_iter);
 }
 
 // sqrt(1 - l^2 - m^2) - 1 in the cancellation-free form -s / (1 + sqrt(1 - s)).
@@ -132,13 +198,22 @@ double dn(double l, double m) {
 }
 
 double wsclean_bound(const double* uvw, int64_t M, double fov_x, double fov_y) {
-    double lo = 0, hi = 0;
-    for (int64_t k = 0; k < M; ++k) {
-        double w = uvw[3 * k + 2];
-        if (k == 0 || w < lo) lo = w;
-        if (k == 0 || w > hi) hi = w;
-    }
-    return 2.0 * M_PI * (hi - lo) * (-dn(0.5 * fov_x, 0.5 * fov_y));
+    const int64_t chunk = 1 << 20, nch = (M + chunk - 1) / chunk;
+    std::vector<double> lo((size_t)nch), hi((size_t)nch);
+    parallel_for(nch, [&](int64_t cb, int64_t ce) {
+        for (int64_t c = cb; c < ce; ++c) {
+            double l = uvw[3 * (c * chunk) + 2], h = l;
+            for (int64_t k = c * chunk; k < std::min(M, (c + 1) * chunk); ++k) {
+                double w = uvw[3 * k + 2];
+                l = std::min(l, w);
+                h = std::max(h, w);
+            }
+            lo[(size_t)c] = l;
+            hi[(size_t)c] = h;
+        }
+    }, 1);
+    double wl = *std::min_element(lo.begin(), lo.end()), wh = *std::max_element(hi.begin(), hi.end());
+    return 2.0 * M_PI * (wh - wl) * (-dn(0.5 * fov_x, 0.5 * fov_y));
 }
 
 static double taper(double lam, double fov) {
@@ -225,9 +300,10 @@ int support_bin(double abs_wr, double wr_max) {
     return q >= N_SUPPORT_BINS - 1 ? N_SUPPORT_BINS - 1 : (int)q;
 }
 
+// w_sub ascending (the subset's order does not change the model).
 static ModelPoint model_for_P(const std::vector<double>& w_sub, int64_t M, int P,
                               const Params& pr) {
-    std::vector<double> c = kmeans1d(w_sub, P, 100);
+    std::vector<double> c = kmeans1d_sorted(w_sub, P, 100);
     int64_t n = (int64_t)w_sub.size();
     std::vector<int32_t> lab(n);
     nearest_all(w_sub.data(), n, 1, c, lab.data());
@@ -269,7 +345,11 @@ Choice choose(const double* uvw, int64_t M, const Params& pr) {
         for (int p : CANDIDATE_P)
             if (p <= std::max(pmax, 1) && p <= std::max<int64_t>(1, ch.subset)) cands.push_back(p);
     }
-    for (int p : cands) ch.models.push_back(model_for_P(w_sub, M, p, pr));
+    std::sort(w_sub.begin(), w_sub.end());
+    ch.models.resize(cands.size());
+    parallel_for((int64_t)cands.size(), [&](int64_t b, int64_t e) {  // independent models
+        for (int64_t i = b; i < e; ++i) ch.models[(size_t)i] = model_for_P(w_sub, M, cands[(size_t)i], pr);
+    }, 1);
     // With an automatic P only bin counts whose residual kernels fit the support cap keep
     // the eta norm fraction (Section 3.1); if none does, the largest candidate truncates
     // least.  A capped support makes K(P) flat in P, so cost alone would pick the fewest

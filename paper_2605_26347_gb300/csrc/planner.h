@@ -54,6 +54,7 @@ std::vector<double> subset_w(const double* uvw, int64_t M, uint64_t seed, double
 void nearest_all(const double* w, int64_t n, int64_t stride, const std::vector<double>& c,
                  int32_t* lab);
 std::vector<double> kmeans1d(const std::vector<double>& w, int P, int max_iter);
+std::vector<double> kmeans1d_sorted(const std::vector<double>& ws, int P, int max_iter);
 double dn(double l, double m);
 double wsclean_bound(const double* uvw, int64_t M, double fov_x, double fov_y);
 int support_at(double w_r, const KernelGeom& g);

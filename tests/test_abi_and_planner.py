@@ -52,6 +52,27 @@ def test_invalid_arguments_are_rejected(rimo_lib):
         assert e.value.status == 1
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf, 2.0 ** 60])
+@pytest.mark.parametrize("col", [0, 1, 2])
+def test_unplaceable_uvw_is_rejected_before_any_device_work(rimo_lib, bad, col):
+    # rimo_plan_create checks the coordinates before it touches a GPU, so both calls
+    # return INVALID_ARG here
+    import ctypes as C
+    import paper_2605_26347_gb300 as pkg
+    uvw = np.ascontiguousarray(synth.make_uvw(5000, 60, 1.28e9, 3))
+    p = _params(pkg, 256, math.radians(1.0), n_wbins=4)
+    uvw[4321, col] = bad
+    with pytest.raises(pkg.RimoError) as e:
+        pkg.estimate(uvw, p)
+    assert e.value.status == 1 and b"uvw" in rimo_lib.rimo_last_error()
+    out = C.c_void_p()
+    st = rimo_lib.rimo_plan_create(uvw.ctypes.data, uvw.shape[0], C.byref(p), None, C.byref(out))
+    assert st == 1 and out.value is None and b"uvw" in rimo_lib.rimo_last_error()
+    # a large but placeable coordinate still plans
+    uvw[4321, col] = 1e12
+    assert pkg.estimate(uvw, p)["P"] == 4
+
+
 @pytest.mark.parametrize("case", [
     dict(n=256, fov=1.0, m=20000, steps=60, seed=1001, bins=4),
     dict(n=256, fov=1.0, m=20000, steps=60, seed=1001, bins=0),
