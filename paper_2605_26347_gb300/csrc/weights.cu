@@ -5,11 +5,14 @@
 // plan rebuilds its tiles with the weights and a plan that generates tiles multiplies them
 // as they are made; the gridding, its fixed-point bounds (taken from the tiles) and H
 // (built from the tiles) follow without further change.
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "internal.h"
+#include "planner.h"
 
 namespace rimo {
 void launch_gbuild(const rimo_plan* p, cudaStream_t s);
@@ -56,23 +59,42 @@ rimo_status rimo_briggs_weights(const double* uvw, int64_t M, int32_t nx, int32_
     if (nx < 1 || ny < 1 || !(fov_x > 0.0) || !(fov_y > 0.0) || !std::isfinite(robust))
         fail(RIMO_ERR_INVALID_ARG, "grid, field of view or robustness out of range");
     if (M == 0) return RIMO_OK;
-    // cell of each visibility on the image's Fourier grid (spacing 1 / FoV), wrapped
+    // cell of each visibility on the image's Fourier grid (spacing 1 / FoV), wrapped; the
+    // visibilities are split over host threads and the per-cell counts are integers, so the
+    // result does not depend on the split
+    const size_t ncell = (size_t)nx * (size_t)ny;
     std::vector<int64_t> cell((size_t)M);
-    std::vector<double> D((size_t)nx * ny, 0.0);
-    for (int64_t k = 0; k < M; ++k) {
-        const double fu = std::floor(uvw[3 * k + 0] * fov_x + 0.5), fv = std::floor(uvw[3 * k + 1] * fov_y + 0.5);
-        if (!std::isfinite(fu) || !std::isfinite(fv)) fail(RIMO_ERR_INVALID_ARG, "non-finite uvw");
-        int64_t cu = (int64_t)std::fmod(fu, (double)nx), cv = (int64_t)std::fmod(fv, (double)ny);
-        if (cu < 0) cu += nx;
-        if (cv < 0) cv += ny;
-        cell[(size_t)k] = cu * ny + cv;
-        D[(size_t)cell[(size_t)k]] += 1.0;
-    }
+    std::unique_ptr<std::atomic<uint64_t>[]> D(new std::atomic<uint64_t>[ncell]());
+    std::atomic<bool> bad{false};
+    planner::parallel_for(M, [&](int64_t b, int64_t e) {
+        bool ok = true;
+        for (int64_t k = b; k < e; ++k) {
+            const double fu = std::floor(uvw[3 * k + 0] * fov_x + 0.5), fv = std::floor(uvw[3 * k + 1] * fov_y + 0.5);
+            if (!std::isfinite(fu) || !std::isfinite(fv)) {
+                ok = false;
+                cell[(size_t)k] = 0;
+                continue;
+            }
+            int64_t cu = (int64_t)std::fmod(fu, (double)nx), cv = (int64_t)std::fmod(fv, (double)ny);
+            if (cu < 0) cu += nx;
+            if (cv < 0) cv += ny;
+            cell[(size_t)k] = cu * ny + cv;
+            D[(size_t)cell[(size_t)k]].fetch_add(1, std::memory_order_relaxed);
+        }
+        if (!ok) bad.store(true);
+    }, 1 << 16);
+    if (bad.load()) fail(RIMO_ERR_INVALID_ARG, "non-finite uvw");
     double sum_d2 = 0.0;
-    for (double d : D) sum_d2 += d * d;
+    for (size_t c = 0; c < ncell; ++c) {
+        const double d = (double)D[c].load(std::memory_order_relaxed);
+        sum_d2 += d * d;
+    }
     const double a = 5.0 * std::pow(10.0, -robust);
     const double f2 = a * a / (sum_d2 / (double)M);
-    for (int64_t k = 0; k < M; ++k) w_out[k] = (float)(1.0 / (1.0 + f2 * D[(size_t)cell[(size_t)k]]));
+    planner::parallel_for(M, [&](int64_t b, int64_t e) {
+        for (int64_t k = b; k < e; ++k)
+            w_out[k] = (float)(1.0 / (1.0 + f2 * (double)D[(size_t)cell[(size_t)k]].load(std::memory_order_relaxed)));
+    }, 1 << 16);
     RIMO_API_END
 }
 
