@@ -1,0 +1,31 @@
+"""Reader of the text fixtures under tests/golden/ ('# ' comment lines, 'key: values')."""
+from __future__ import annotations
+
+import os
+from fractions import Fraction
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load(name: str) -> dict[str, str]:
+    out = {}
+    with open(os.path.join(GOLDEN, name), encoding="utf-8") as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, _, val = line.partition(":")
+            out[key.strip()] = val.strip()
+    return out
+
+
+def numbers(text: str) -> list[float]:
+    """Whitespace-separated numbers; 'a/b' is an exact ratio evaluated once."""
+    vals = []
+    for tok in text.split():
+        if "/" in tok:
+            num, den = tok.split("/")
+            vals.append(float(Fraction(num) / Fraction(den)))
+        else:
+            vals.append(float(tok))
+    return vals

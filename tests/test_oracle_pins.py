@@ -11,6 +11,7 @@ import pytest
 import scipy.integrate as si
 import scipy.special as ss
 
+import golden_data
 import synth
 from oracle import direct, kb, operator, plan as pl, wterm
 
@@ -237,12 +238,11 @@ def test_support_table_monotone_and_eta_one_is_max():
 
 
 def test_splitmix64_published_sequence():
-    # Vigna's reference splitmix64 with seed 1234567
-    k = np.arange(1, 6, dtype=np.uint64)
-    out = pl.splitmix64(np.uint64(1234567) + k * np.uint64(pl.GOLDEN))
-    assert list(map(int, out)) == [6457827717110365317, 3203168211198807973,
-                                   9817491932198370423, 4593380528125082431,
-                                   16408922859458223821]
+    g = golden_data.load("splitmix64_seed1234567.txt")
+    expect = [int(v) for v in g["outputs"].split()]
+    k = np.arange(1, len(expect) + 1, dtype=np.uint64)
+    out = pl.splitmix64(np.uint64(int(g["state"])) + k * np.uint64(pl.GOLDEN))
+    assert list(map(int, out)) == expect
 
 
 def test_kmeans_recovers_separated_clusters():

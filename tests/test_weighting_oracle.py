@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 
+import golden_data
 import synth
 from oracle import direct, operator, plan as pl, weighting
 
@@ -32,14 +33,13 @@ def make_op(uvw, n, fov, weights=None, **kw):
 
 # ---------------------------------------------------------------- Briggs weights
 def test_briggs_hand_worked_example():
-    # two visibilities in cell (0, 0), one in cell (3, 0) of an 8 x 8 grid, FoV = 1:
-    # D = (2, 1), sum D^2 / M = 5 / 3.  R = 0: f^2 = 25 * 3 / 5 = 15, w = 1/31, 1/31, 1/16.
-    # R = 1: f^2 = 0.25 * 3 / 5 = 0.15, w = 1/1.3, 1/1.3, 1/1.15.
-    uvw = np.array([[0.1, 0.2, 0.0], [0.3, -0.1, 0.0], [2.6, 0.0, 0.0]])
-    w0 = weighting.briggs_weights(uvw, 8, 8, 1.0, 1.0, 0.0)
-    assert np.allclose(w0, [1 / 31, 1 / 31, 1 / 16], rtol=1e-15, atol=0)
-    w1 = weighting.briggs_weights(uvw, 8, 8, 1.0, 1.0, 1.0)
-    assert np.allclose(w1, [1 / 1.3, 1 / 1.3, 1 / 1.15], rtol=1e-15, atol=0)
+    g = golden_data.load("briggs_three_visibilities.txt")
+    nx, ny = (int(v) for v in g["grid"].split())
+    fx, fy = golden_data.numbers(g["fov"])
+    uvw = np.array([golden_data.numbers(r) for r in g["uvw"].split("|")])
+    for R in (0, 1):
+        w = weighting.briggs_weights(uvw, nx, ny, fx, fy, float(R))
+        assert np.allclose(w, golden_data.numbers(g[f"weights R={R}"]), rtol=1e-15, atol=0)
 
 
 def test_briggs_natural_and_uniform_limits():
