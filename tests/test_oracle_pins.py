@@ -120,6 +120,17 @@ def test_widefield_error_falls_with_kernel_support():
     assert errs[-1] < 1e-4
 
 
+def test_widefield_error_falls_with_wkernel_sampling_when_support_allows():
+    # Section 3.1: the w-kernel is the DFT of the chirp sampled on an L x L grid over twice
+    # the FoV; with a support wide enough not to cut it, a finer grid lowers the error
+    # until the NUFFT error dominates (with 9 taps the support cut dominates at every L)
+    n = 32
+    uvw, x, fov = small_case(m=300, n=n, w_scale=0.01)
+    yd = direct.direct_phi(x, uvw, fov, fov)
+    errs = [rel(make_op(uvw, n, fov, max_wsupport=31, wkernel_L=L).phi(x), yd) for L in (32, 64, 128)]
+    assert errs[1] < 0.7 * errs[0] and errs[2] < errs[1], errs
+
+
 def test_div_n_option_matches_eq2_with_one_over_n():
     n = 32
     uvw, x, fov = small_case(m=200, n=n, w_scale=0.0)
