@@ -97,6 +97,41 @@ def test_planner_matches_oracle(case):
     assert abs(est["wsclean_p"] - opl.wsclean_bound(uvw[:, 2], fov, fov)) < 1e-9 * est["wsclean_p"]
 
 
+def _random_cases(n_cases, seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(n_cases):
+        yield dict(n=int(rng.choice([64, 128, 256, 512, 1024])), nyf=int(rng.choice([1, 2])),
+                   fov=float(rng.uniform(0.5, 4.0)), m=int(rng.integers(500, 60000)),
+                   steps=int(rng.choice([60, 600, 28800])), seed=int(rng.integers(1, 10**6)),
+                   bins=int(rng.choice([0, 0, int(rng.integers(1, 48))])),
+                   J=int(rng.choice([5, 7, 9])), Sw=int(rng.choice([3, 5, 7, 9])),
+                   frac=float(rng.choice([0.01, 0.05, 0.3])), pseed=int(rng.integers(0, 2**40)),
+                   budget_frac=float(rng.choice([0.0, 0.5, 1.0, 2.0])))
+
+
+@pytest.mark.parametrize("case", list(_random_cases(10, 2024)), ids=lambda c: f"n{c['n']}-m{c['m']}-P{c['bins']}")
+def test_planner_matches_oracle_on_random_workloads(case):
+    # every planning decision of the host planner (k-means on the sorted subset, per-P
+    # models in parallel) against the oracle's plain implementation
+    import paper_2605_26347_gb300 as pkg
+    uvw = synth.make_uvw(case["m"], case["steps"], 1.28e9, case["seed"])
+    nx = case["n"]
+    ny = max(64, nx // case["nyf"])
+    fx = math.radians(case["fov"])
+    fy = fx * ny / nx
+    kw = dict(n_wbins=case["bins"], kb_support=case["J"], max_wsupport=case["Sw"],
+              plan_fraction=case["frac"], seed=case["pseed"])
+    ref0 = opl.choose(uvw, opl.PlanParams(nx=nx, ny=ny, fov_x=fx, fov_y=fy, **kw))
+    budget = int(case["budget_frac"] * min(d["m_G"] for d in ref0["models"]))
+    ref = opl.choose(uvw, opl.PlanParams(nx=nx, ny=ny, fov_x=fx, fov_y=fy, mem_budget_bytes=budget, **kw))
+    est = pkg.estimate(uvw, pkg.default_params(nx, ny, fx, fy, mem_budget_bytes=budget, **kw))
+    assert (est["P"], est["mode"], est["p_star"], est["subset"]) == (ref["P"], ref["mode"], ref["p_star"], ref["subset"])
+    m = {d["P"]: d for d in ref["models"]}[est["P"]]
+    assert abs(est["est_m_g"] - m["m_G"]) <= 1e-9 * m["m_G"]
+    assert abs(est["est_cost"] - m["cost"]) <= 1e-9 * m["cost"]
+    assert est["truncated"] == int(m["truncated"])
+
+
 def test_planner_budget_regimes_match_oracle():
     # Fig. 2 regimes forced by the budget: stored G at P*, nearest feasible P, holographic
     import paper_2605_26347_gb300 as pkg
