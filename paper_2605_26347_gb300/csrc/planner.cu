@@ -20,10 +20,14 @@ int hw_threads() {
     return n == 0 ? 1 : (int)std::min(n, 64u);
 }
 
+// Set in the worker threads of parallel_for: a parallel_for called from one of them runs
+// serially, so nested loops never multiply the thread count.
+static thread_local bool tl_worker = false;
+
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f, int64_t min_chunk) {
     int T = hw_threads();
     int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(T, n / std::max<int64_t>(1, min_chunk)));
-    if (chunks <= 1) {
+    if (chunks <= 1 || tl_worker) {
         f(0, n);
         return;
     }
@@ -31,7 +35,11 @@ void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f, int
     int64_t step = (n + chunks - 1) / chunks;
     for (int64_t c = 0; c < chunks; ++c) {
         int64_t b = c * step, e = std::min(n, b + step);
-        if (b < e) th.emplace_back(f, b, e);
+        if (b < e)
+            th.emplace_back([&f](int64_t lo, int64_t hi) {
+                tl_worker = true;
+                f(lo, hi);
+            }, b, e);
     }
     for (auto& t : th) t.join();
 }
