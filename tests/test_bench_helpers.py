@@ -1,5 +1,6 @@
 """Host logic of bench.py: the capture-staleness digest, the committed traffic lookup and
 the algorithmic byte counts (CPU only)."""
+import argparse
 import json
 import os
 import shutil
@@ -7,6 +8,10 @@ import shutil
 import pytest
 
 import bench
+
+
+def argparse_ns(n, m, bins):
+    return argparse.Namespace(n=n, m=m, bins=bins)
 
 
 def test_code_digest_ignores_comments_and_whitespace(tmp_path):
@@ -45,3 +50,30 @@ def test_apply_bytes_follow_the_stage_sum():
     assert sb["apply_per_step"] == pytest.approx(8 * info["K"] + 16 * M + 3 * patches + P * 120 * n * n)
     per_bin_fft = sb["fwd_rows"] + sb["fwd_cols"] + sb["inv_rows"]
     assert sb["apply_per_step"] == pytest.approx(sb["gtg_per_step"] + sb["inv_cols_per_step"] + P * per_bin_fft)
+
+
+def test_workload_label_names_the_sizes_run():
+    full, small = argparse_ns(4096, 50_000_000, 32), argparse_ns(256, 20000, 4)
+    assert bench.workload_name(full) == bench.WORKLOAD
+    assert "256x256 image" in bench.workload_name(small) and "20000 visibilities" in bench.workload_name(small)
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm times the FP64 oracle on the host cores (no GPU involved)
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--n", "256", "--m", "20000", "--bins", "4", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["ms_per_step"] == pytest.approx(1000.0 / d["value"])
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 1, 0)
+    assert d["config"]["workload"] == bench.workload_name(argparse_ns(256, 20000, 4))
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
