@@ -180,6 +180,45 @@ rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_param
 /* Free a plan and all device memory it owns.  NULL is accepted. */
 rimo_status rimo_plan_destroy(rimo_plan_t plan);
 
+/*
+ * Plan files (Section 4: the planning stage may run on its own, and both stages read one
+ * parameter file and one observation file of (u, v, w) coordinates).  A plan is fully
+ * determined by its coordinates and parameters, so a plan file holds those - and the data
+ * weights injected into the operator, if any (Section 2) - and rimo_plan_create_from_file
+ * rebuilds the identical plan in another process or later.  Format: an 8-byte magic
+ * "RIMOPLAN", format version 1, sizeof(rimo_plan_params), M, a weights flag, the
+ * parameters, uvw (M x 3 float64), the weights (M float32) when present, and a 64-bit
+ * FNV-1a checksum of every byte before it (per 1 MiB block, then over the block digests);
+ * little-endian, the byte order of the machines this library builds for.
+ */
+
+/*
+ * Write a plan file.  uvw: host, M x 3 row-major float64 (wavelengths); p: the plan
+ * parameters; weights: host, M float32 (finite, >= 0) or NULL for none.  Host only (no GPU).
+ * The caller's arrays are read, not retained; an existing file is replaced.
+ * Errors: INVALID_ARG (null pointer, M out of range, parameters or coordinates that
+ * rimo_plan_create would refuse, bad weights, a path that cannot be written).
+ */
+rimo_status rimo_plan_file_write(const char* path, const double* uvw, int64_t M, const rimo_plan_params* p,
+                                 const float* weights);
+
+/*
+ * Read and check a whole plan file (magic, version, sizes, checksum, parameters,
+ * coordinates, weights) and report its parameters, M and whether it holds weights (any
+ * output may be NULL).  Host only.  Errors: INVALID_ARG naming the first check that failed
+ * (a corrupted, truncated or foreign file among them).
+ */
+rimo_status rimo_plan_file_info(const char* path, rimo_plan_params* p, int64_t* M, int32_t* has_weights);
+
+/*
+ * Create the plan a plan file describes: the checks of rimo_plan_file_info, then
+ * rimo_plan_create on its coordinates and parameters, then rimo_plan_set_weights with its
+ * weights when it holds them.  Streams and synchronisation as rimo_plan_create.
+ * Errors: those of rimo_plan_file_info, rimo_plan_create and rimo_plan_set_weights; on
+ * failure *out is NULL and nothing stays allocated.
+ */
+rimo_status rimo_plan_create_from_file(const char* path, void* stream, rimo_plan_t* out);
+
 /* Copy the plan summary into *info (host). */
 rimo_status rimo_plan_info_get(rimo_plan_t plan, rimo_plan_info* info);
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 
 import numpy as np
 
@@ -78,6 +79,20 @@ class Plan:
         _lib.check(self._lib.rimo_plan_create(u.ctypes.data, self.M, C.byref(params),
                                               _stream_ptr(stream), C.byref(h)))
         self._h = h
+
+    @classmethod
+    def from_file(cls, path: str, stream=None) -> "Plan":
+        """rimo_plan_create_from_file: the plan a plan file (write_plan_file) describes."""
+        params, M, _ = plan_file_info(path)
+        self = cls.__new__(cls)
+        self._lib = _lib.load()
+        self.params = params
+        self.nx, self.ny = int(params.nx), int(params.ny)
+        self.M = M
+        h = C.c_void_p()
+        _lib.check(self._lib.rimo_plan_create_from_file(os.fsencode(path), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        return self
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -365,6 +380,30 @@ def image_dot(a, b, stream=None) -> float:
     r = C.c_double()
     _lib.check(lib.rimo_image_dot(a.data_ptr(), b.data_ptr(), a.numel(), C.byref(r), _stream_ptr(stream)))
     return r.value
+
+
+def write_plan_file(path: str, uvw, params: PlanParams, weights=None) -> None:
+    """rimo_plan_file_write: the inputs of a plan (uvw, parameters, optional data weights)
+    in one checked file; host only."""
+    lib = _lib.load()
+    u = _uvw_arg(uvw)
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
+        if w.size != u.shape[0]:
+            raise ValueError(f"expected {u.shape[0]} weights, got {w.size}")
+    _lib.check(lib.rimo_plan_file_write(os.fsencode(path), u.ctypes.data, u.shape[0], C.byref(params),
+                                        None if w is None else w.ctypes.data))
+
+
+def plan_file_info(path: str) -> tuple[PlanParams, int, bool]:
+    """rimo_plan_file_info: (parameters, M, holds weights) of a checked plan file; host only."""
+    lib = _lib.load()
+    p = PlanParams()
+    M = C.c_int64()
+    hw = C.c_int32()
+    _lib.check(lib.rimo_plan_file_info(os.fsencode(path), C.byref(p), C.byref(M), C.byref(hw)))
+    return p, int(M.value), bool(hw.value)
 
 
 def briggs_weights(uvw, nx: int, ny: int, fov_x: float, fov_y: float, robust: float) -> np.ndarray:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librimo.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["planner.cu", "plan.cu", "fft.cu", "grid.cu", "gbuild.cu", "apply.cu", "noalloc.cu", "mlp.cu", "batch.cu", "hmat.cu", "weights.cu", "fb.cu"]
+SOURCES = ["planner.cu", "plan.cu", "fft.cu", "grid.cu", "gbuild.cu", "apply.cu", "noalloc.cu", "mlp.cu", "batch.cu", "hmat.cu", "weights.cu", "fb.cu", "planfile.cu"]
 
 
 def nvcc() -> str:

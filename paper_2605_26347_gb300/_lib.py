@@ -116,6 +116,9 @@ _PROTOS = {
     "rimo_briggs_weights": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P]),
     "rimo_fb_step": (C.c_int, [_P, _P, _P, C.c_float, _P, C.c_int64, _P]),
     "rimo_image_dot": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_double), _P]),
+    "rimo_plan_file_write": (C.c_int, [C.c_char_p, _P, C.c_int64, C.POINTER(PlanParams), _P]),
+    "rimo_plan_file_info": (C.c_int, [C.c_char_p, C.POINTER(PlanParams), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "rimo_plan_create_from_file": (C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     "rimo_last_error": (C.c_char_p, []),
     "rimo_version": (C.c_char_p, []),
 }

@@ -36,6 +36,9 @@ void set_last_error(const std::string& msg);
     }
 [[noreturn]] void fail(rimo_status s, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+// Parameter and coordinate checks of plan creation (RIMO_ERR_INVALID_ARG on failure).
+void validate_params(const rimo_plan_params& q);
+void validate_uvw(const double* uvw, int64_t M, const rimo_plan_params& q);
 #define RIMO_CUDA(call) ::rimo::check_cuda((call), #call)
 
 // ---------------------------------------------------------------------------

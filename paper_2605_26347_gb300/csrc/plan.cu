@@ -72,7 +72,7 @@ static double kb_hat(double nu, int J, double beta) {
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-static void validate(const rimo_plan_params& q) {
+void validate_params(const rimo_plan_params& q) {
     auto bad = [](const std::string& m) { fail(RIMO_ERR_INVALID_ARG, m); };
     if (!is_pow2(q.nx) || !is_pow2(q.ny) || q.nx < 64 || q.ny < 64 || q.nx > 4096 || q.ny > 4096)
         bad("nx and ny must be powers of two in [64, 4096]");
@@ -99,7 +99,7 @@ static void validate(const rimo_plan_params& q) {
 // Every coordinate finite and within the range where the placement (floor, integer
 // conversion, wrap) and the k-means sums stay exact: |u| 2 fov_x, |v| 2 fov_y and |w|
 // below 2^52.  Checked in parallel; the error is raised on the calling thread.
-static void validate_uvw(const double* uvw, int64_t M, const rimo_plan_params& q) {
+void validate_uvw(const double* uvw, int64_t M, const rimo_plan_params& q) {
     const double lim = 0x1.0p52;
     std::atomic<bool> bad{false};
     planner::parallel_for(M, [&](int64_t b, int64_t e) {
@@ -242,7 +242,7 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q, cudaStream_t s,
                         rimo_plan* p) {
-    validate(q);
+    validate_params(q);
     p->prm = q;
     p->nx = q.nx;
     p->ny = q.ny;
@@ -650,7 +650,7 @@ rimo_status rimo_plan_estimate(const double* uvw, int64_t M, const rimo_plan_par
                                rimo_plan_info* info) {
     try {
         if (!uvw || M <= 0 || !q || !info) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
-        validate(*q);
+        validate_params(*q);
         validate_uvw(uvw, M, *q);
         planner::Params pr = planner_params(*q);
         planner::Choice ch = planner::choose(uvw, M, pr);
@@ -673,7 +673,7 @@ rimo_status rimo_plan_create(const double* uvw, int64_t M, const rimo_plan_param
     try {
         if (!uvw || M <= 0 || !q || !out) fail(RIMO_ERR_INVALID_ARG, "null pointer or M <= 0");
         if (M > 2000000000LL) fail(RIMO_ERR_INVALID_ARG, "M above 2e9 visibilities");
-        validate(*q);
+        validate_params(*q);
         validate_uvw(uvw, M, *q);
         p = new rimo_plan();
         create_plan(uvw, M, *q, (cudaStream_t)stream, p);
