@@ -37,9 +37,18 @@ def _flags(verbose_ptxas: bool = False) -> list[str]:
     return f
 
 
-def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose_ptxas)
+# Host-side AddressSanitizer + UBSan build of the same sources (device code unchanged), for
+# checking the host code (planner, plan files, weights, argument checks); it is loaded with
+# RIMO_LIBRARY=<its path> and the two sanitizer runtimes preloaded.
+SAN_BUILD = os.path.join(BUILD, "san")
+SAN_LIB = os.path.join(HERE, "librimo_san.so")
+SAN_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+             "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-g"]
+
+
+def _compile(src: str, verbose_ptxas: bool, sanitize: bool = False) -> tuple[str, str]:
+    obj = os.path.join(SAN_BUILD if sanitize else BUILD, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose_ptxas) + (SAN_FLAGS if sanitize else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -54,25 +63,27 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) -> str:
-    """Compile all sources and link librimo.so; returns its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True, sanitize: bool = False) -> str:
+    """Compile all sources and link librimo.so (librimo_san.so with sanitize); returns its path."""
+    lib = SAN_LIB if sanitize else LIB
+    if not sanitize and not force and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(SAN_BUILD if sanitize else BUILD, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, verbose_ptxas, sanitize), SOURCES))
     if verbose_ptxas or not quiet:
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"]
+    tmp = lib + ".tmp"
+    cmd = [nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"] + (SAN_FLAGS if sanitize else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, quiet=False))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, quiet=False,
+                sanitize="--sanitize" in sys.argv))

@@ -9,7 +9,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librimo.so")
+# RIMO_LIBRARY selects another build of the same library (the sanitizer build, for one)
+LIB_PATH = os.environ.get("RIMO_LIBRARY") or os.path.join(HERE, "librimo.so")
 
 RIMO_OK = 0
 N_STAGES = 16
