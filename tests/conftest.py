@@ -15,6 +15,9 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def rimo_lib():
-    """The compiled CUDA library (built on demand by the build helper)."""
-    from paper_2605_26347_gb300 import _lib
+    """The compiled CUDA library, built first (nvcc) when it is missing or older than its
+    sources.  Host-only entry points run without a GPU."""
+    from paper_2605_26347_gb300 import _build, _lib
+    if _lib.LIB_PATH == _build.LIB:  # not when RIMO_LIBRARY selects another build
+        _build.build()
     return _lib.load()

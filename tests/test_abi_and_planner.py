@@ -79,7 +79,7 @@ def test_unplaceable_uvw_is_rejected_before_any_device_work(rimo_lib, bad, col):
     dict(n=512, fov=2.5, m=60000, steps=28800, seed=77, bins=0, budget=0),
     dict(n=1024, fov=2.5, m=200000, steps=28800, seed=1002, bins=0, budget=40 * 2**30),
 ])
-def test_planner_matches_oracle(case):
+def test_planner_matches_oracle(case, rimo_lib):
     import paper_2605_26347_gb300 as pkg
     uvw = synth.make_uvw(case["m"], case["steps"], 1.28e9, case["seed"])
     fov = math.radians(case["fov"])
@@ -110,7 +110,7 @@ def _random_cases(n_cases, seed):
 
 
 @pytest.mark.parametrize("case", list(_random_cases(10, 2024)), ids=lambda c: f"n{c['n']}-m{c['m']}-P{c['bins']}")
-def test_planner_matches_oracle_on_random_workloads(case):
+def test_planner_matches_oracle_on_random_workloads(case, rimo_lib):
     # every planning decision of the host planner (k-means on the sorted subset, per-P
     # models in parallel) against the oracle's plain implementation
     import paper_2605_26347_gb300 as pkg
@@ -132,7 +132,7 @@ def test_planner_matches_oracle_on_random_workloads(case):
     assert est["truncated"] == int(m["truncated"])
 
 
-def test_planner_budget_regimes_match_oracle():
+def test_planner_budget_regimes_match_oracle(rimo_lib):
     # Fig. 2 regimes forced by the budget: stored G at P*, nearest feasible P, holographic
     import paper_2605_26347_gb300 as pkg
     uvw = synth.make_uvw(30000, 60, 1.28e9, 5)
@@ -145,7 +145,7 @@ def test_planner_budget_regimes_match_oracle():
         assert (est["P"], est["mode"]) == (r["P"], r["mode"]), budget
 
 
-def test_briggs_weights_match_oracle_on_the_host():
+def test_briggs_weights_match_oracle_on_the_host(rimo_lib):
     # host logic of the library (no GPU): Briggs' robust weights against the oracle's
     import paper_2605_26347_gb300 as pkg
     from oracle import weighting
@@ -163,7 +163,7 @@ def test_briggs_weights_match_oracle_on_the_host():
         pkg.briggs_weights(bad, 128, 96, fov, fov, 0.0)
 
 
-def test_python_structures_match_the_c_header(tmp_path):
+def test_python_structures_match_the_c_header(tmp_path, rimo_lib):
     # the ctypes views of rimo_plan_params and rimo_plan_info against the header's layout,
     # compiled by the host C compiler (sizes and every field offset)
     import ctypes as C
