@@ -193,3 +193,16 @@ def test_python_structures_match_the_c_header(tmp_path, rimo_lib):
         assert C.sizeof(py) == want[(cname, "size")], cname
         for f, _ in py._fields_:
             assert getattr(py, f).offset == want[(cname, f)], (cname, f)
+
+
+def test_product_path_fails_loudly_without_the_library(tmp_path):
+    # no fallback: every entry point needs librimo.so, and its absence is an ImportError
+    import subprocess
+    import sys
+    code = ("import math, numpy as np, paper_2605_26347_gb300 as pkg\n"
+            "uvw = np.zeros((10, 3))\n"
+            "pkg.estimate(uvw, pkg.default_params(64, 64, 0.01, 0.01))\n")
+    env = dict(os.environ, RIMO_LIBRARY=str(tmp_path / "librimo.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "build the CUDA library first" in r.stderr
