@@ -97,6 +97,31 @@ def test_damaged_files_are_refused_before_any_device_work(tmp_path, rimo_lib):
         pkg.plan_file_info(str(tmp_path / "missing.rimoplan"))
 
 
+def test_well_formed_files_with_bad_contents_are_refused(tmp_path, rimo_lib):
+    # a valid checksum over contents that plan creation would refuse: the file is checked
+    # like the arguments of rimo_plan_create after its checksum
+    pkg, uvw, params, w = _case()
+    good = tmp_path / "good.rimoplan"
+    pkg.write_plan_file(str(good), uvw, params, weights=w)
+    raw = bytearray(good.read_bytes())
+    psize = C.sizeof(pkg.PlanParams)
+    M = uvw.shape[0]
+    bad_params = pkg.PlanParams.from_buffer_copy(bytes(raw[32:32 + psize]))
+    bad_params.nx = 100
+    edits = {"nx and ny": (32, bytes(bad_params)),
+             "non-finite": (32 + psize + 24 * 11 + 16, struct.pack("<d", float("nan"))),
+             "weights must be": (32 + psize + 24 * M + 4 * 9, struct.pack("<f", -0.5))}
+    for why, (off, data) in edits.items():
+        buf = bytearray(raw)
+        buf[off:off + len(data)] = data
+        buf[-8:] = struct.pack("<Q", documented_checksum(bytes(buf[:-8])))
+        path = tmp_path / "edited.rimoplan"
+        path.write_bytes(bytes(buf))
+        with pytest.raises(pkg.RimoError) as e:
+            pkg.plan_file_info(str(path))
+        assert e.value.status == 1 and why in str(e.value), (why, str(e.value))
+
+
 def test_write_refuses_what_plan_creation_would(tmp_path, rimo_lib):
     pkg, uvw, params, w = _case()
     path = str(tmp_path / "x.rimoplan")
