@@ -29,3 +29,17 @@ def numbers(text: str) -> list[float]:
         else:
             vals.append(float(tok))
     return vals
+
+
+def entries(name: str, key: str) -> list[str]:
+    """Every value of a key that appears on several lines, in file order."""
+    out = []
+    with open(os.path.join(GOLDEN, name), encoding="utf-8") as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, _, val = line.partition(":")
+            if k.strip() == key:
+                out.append(val.strip())
+    return out
