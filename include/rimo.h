@@ -338,7 +338,15 @@ rimo_status rimo_profile_read(rimo_plan_t plan, double* ms, int64_t* launches, i
  * forward / gridded grid, the tile patches, the tile schedulers) from one array of
  * RIMO_NOALLOC_SCRATCH_BYTES (32 MiB) that the library allocates statically on every
  * device that loads it and keeps until the process exits.  The call itself performs no
- * cudaMalloc, cudaFree or other allocating call; the plan's own memory is only read.
+ * cudaMalloc, cudaFree or other allocating call.  Of the plan's own device memory it
+ * writes only the status word (read by rimo_plan_status) and the grid step's bound
+ * words, as the regular apply does; for the duration of the call the plan's scratch
+ * pointers are pointed at the array (and restored before it returns), so the plan must
+ * not be applied from another thread meanwhile (plans are not re-entrant in any case).
+ * Nothing of the array needs clearing between calls or between plans: the tile
+ * schedulers are reset by every apply, and every grid cell an apply reads was written
+ * earlier in the same apply (the forward column pass writes every cell of every uv-tile
+ * that some tile patch of the bin reaches, which is every cell the grid step stages).
  *
  * Limit: the plan must fit the array: 8 (6 nx ny + max tiles per w-bin * (TS + H)^2) bytes
  * plus a little alignment, about nx = ny = 512 at most; larger plans are rejected with

@@ -28,7 +28,7 @@ from . import kb as kbm
 from . import wterm
 from .plan import Plan
 
-CHUNK = 2048
+CHUNK = 256  # visibilities per vectorised step (small arrays stay in cache)
 
 
 def _workers() -> int:
@@ -58,10 +58,23 @@ class Geometry:
         self.S = plan.s_w + J - 1
 
 
+_POOL_OP = None
+
+
+def _pool_init(op) -> None:
+    global _POOL_OP
+    _POOL_OP = op
+
+
+def _pool_tiles(idx: np.ndarray) -> list[np.ndarray]:
+    return _POOL_OP.tiles(idx)
+
+
 class Operator:
     """The discrete hybrid w-stacking / w-projection operator of one plan."""
 
-    def __init__(self, uvw: np.ndarray, plan: Plan, build_g: bool = True, weights=None):
+    def __init__(self, uvw: np.ndarray, plan: Plan, build_g: bool = True, weights=None,
+                 workers: int = 1):
         self.uvw = np.asarray(uvw, dtype=np.float64)
         # diagonal data weighting W (None: W = I)
         self.w = None if weights is None else np.asarray(weights, dtype=np.float64)
@@ -78,7 +91,9 @@ class Operator:
         self.M = self.uvw.shape[0]
         self.G = None
         if build_g:
-            self.G = [self._build_g(p) for p in range(plan.P)]
+            # tiles of every visibility (in caller order), then one sparse G_p per bin
+            allt = self.tiles_parallel(np.arange(self.M), workers)
+            self.G = [self._build_g(p, allt) for p in range(plan.P)]
 
     # ---- Z_p ------------------------------------------------------------
     def z_layer(self, p: int) -> np.ndarray:
@@ -114,15 +129,29 @@ class Operator:
                     out[j] = T[q]
         return out  # type: ignore[return-value]
 
+    def tiles_parallel(self, idx: np.ndarray, workers: int = 1) -> list[np.ndarray]:
+        """tiles(idx) computed by `workers` processes over contiguous slices of idx (the
+        same arithmetic per visibility; a spawned pool, safe after CUDA was initialised)."""
+        idx = np.asarray(idx, dtype=np.int64)
+        if workers <= 1 or idx.size < 8 * CHUNK:
+            return self.tiles(idx)
+        import multiprocessing as mp
+        light = object.__new__(Operator)
+        light.__dict__.update({k: v for k, v in self.__dict__.items() if k not in ("G", "gc")})
+        parts = np.array_split(idx, 4 * workers)
+        with mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(light,)) as pool:
+            res = pool.map(_pool_tiles, parts)
+        return [t for r in res for t in r]
+
     def tile_cells(self, k: int):
         """Grid cells (g_u, g_v) touched by visibility k, each (S,) modulo the grid."""
         S = int(self.geo.S[k])
         a = np.arange(S)
         return (self.geo.g0[k] + a) % self.gx, (self.geo.h0[k] + a) % self.gy
 
-    def _build_g(self, p: int) -> sp.csr_matrix:
+    def _build_g(self, p: int, all_tiles=None) -> sp.csr_matrix:
         rows_k = np.nonzero(self.plan.bins == p)[0]
-        Ts = self.tiles(rows_k)
+        Ts = self.tiles(rows_k) if all_tiles is None else [all_tiles[k] for k in rows_k]
         r, c, v = [], [], []
         for q, k in enumerate(rows_k):
             cu, cv = self.tile_cells(int(k))

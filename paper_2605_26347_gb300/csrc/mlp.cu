@@ -39,8 +39,25 @@ __device__ __forceinline__ float erf_as(float x) {
 // GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 (the network's activation everywhere it
 // runs forward: training, batched forward, tile generation)
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erf_as(z * 0.70710678118654752f)); }
+// derivative of that same function (training follows the gradient of the GELU the network
+// evaluates): with x = z / sqrt 2, E = erf_as and t, poly as in erf_as,
+// dE/dx = e^{-x^2} (2 |x| poly(t) + p t^2 poly'(t)) (even in x), so
+// GELU'(z) = (1 + E(x)) / 2 + z dE/dx / (2 sqrt 2).
 __device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const float x = z * 0.70710678118654752f;
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    // d poly / dt = a1 + 2 a2 t + 3 a3 t^2 + 4 a4 t^3 + 5 a5 t^4
+    const float dpoly =
+        fmaf(t, fmaf(t, fmaf(t, fmaf(t, 5.f * 1.061405429f, 4.f * -1.453152027f), 3.f * 1.421413741f),
+                     2.f * -0.284496736f),
+             0.254829592f);
+    const float e = __expf(-ax * ax);
+    const float E = copysignf(fmaf(-poly, e, 1.f), x);
+    const float dE = e * fmaf(2.f * ax, poly, 0.3275911f * t * t * dpoly);
+    return fmaf(0.5f, 1.f + E, z * dE * 0.35355339059327376f);
 }
 
 __device__ __forceinline__ void mbar_init_(uint64_t* bar, uint32_t count) {

@@ -64,7 +64,13 @@ extern "C" rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t p, const rimo_
                                            std::to_string(NOALLOC_BYTES) + "-byte static scratch");
         unsigned char* base = noalloc_scratch();
         cudaStream_t s = (cudaStream_t)stream;
-        // run the regular apply with the plan's scratch pointers pointed into the array
+        // run the regular apply with the plan's scratch pointers pointed into the array.
+        // The array keeps the previous call's contents (possibly another plan's layout);
+        // none of it is read before this apply writes it: the schedulers are cleared by
+        // the apply itself, the forward column pass writes every cell of every needed
+        // uv-tile (the tiles any active patch of the bin reaches, a superset of the cells
+        // the grid step stages), the fold writes the needed tiles of the gridded grid, and
+        // the inverse column pass reads needed tiles only.
         int32_t* own_counter = p->d_counter;
         float2* own_ab = p->d_AB;
         float2* own_x = p->d_X;
