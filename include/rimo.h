@@ -374,6 +374,21 @@ rimo_status rimo_apply_phi_adj_phi_noalloc(rimo_plan_t plan, const rimo_cfloat* 
 rimo_status rimo_plan_status(rimo_plan_t plan, void* stream);
 
 /*
+ * Failure-detection test of the device-side bounded waits (no counterpart in the paper;
+ * the paper's workers fail on the host).  With stall = 1, the grid-step launches of this
+ * plan's following applies run with their consumer warps never releasing a ring slot of
+ * taps to the producer warp (a flag that nothing sets), and the producer's waits on the
+ * other warps limited to `polls` (1 .. 32768) suspended polls of at most 100 us.  A block
+ * whose producer has to reuse a slot then gives up: it records RIMO_ERR_TIMEOUT in the
+ * plan's status, waits (with the normal bound) for its own bulk copies in flight, and
+ * returns, and its consumer warps stop waiting for chunks that will not come.  Results of
+ * applies made with stall = 1 are invalid; rimo_plan_status reports the timeout.
+ * stall = 0 (polls ignored) restores normal operation.  Host-only call.
+ * Errors: INVALID_ARG.
+ */
+rimo_status rimo_plan_set_wait_test(rimo_plan_t plan, int32_t stall, int32_t polls);
+
+/*
  * Kernel surrogate (a learned replacement for the stored de-gridding taps; no
  * counterpart in the paper, which stores G or H or recomputes G on the fly, Section 3.4).
  * A multilayer perceptron maps the normalised inputs x = (2 phi_u - 1, 2 phi_v - 1,

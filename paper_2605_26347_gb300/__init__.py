@@ -181,6 +181,15 @@ class Plan:
         _lib.check(self._lib.rimo_profile_read(self._h, ms, ln, _lib.N_STAGES, int(reset)))
         return {name: (ms[i], ln[i]) for i, name in enumerate(_lib.STAGE_NAMES)}
 
+    def status(self, stream=None) -> None:
+        """Raise RimoError if a kernel of this plan gave up a bounded wait (TIMEOUT) or met a
+        non-finite input (INVALID_ARG) since the last check (rimo_plan_status)."""
+        _lib.check(self._lib.rimo_plan_status(self._h, _stream_ptr(stream)))
+
+    def set_wait_test(self, stall: bool, polls: int = 16) -> None:
+        """Failure-detection test of the grid step's bounded waits (rimo_plan_set_wait_test)."""
+        _lib.check(self._lib.rimo_plan_set_wait_test(self._h, int(bool(stall)), int(polls)))
+
     def build_holographic(self, stream=None):
         _lib.check(self._lib.rimo_build_holographic(self._h, _stream_ptr(stream)))
 

@@ -95,6 +95,7 @@ _PROTOS = {
     "rimo_plan_get_holographic": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, _P]),
     "rimo_psf": (C.c_int, [_P, _P, _P]),
     "rimo_plan_status": (C.c_int, [_P, _P]),
+    "rimo_plan_set_wait_test": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "rimo_profile_enable": (C.c_int, [_P, C.c_int32]),
     "rimo_profile_read": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
     "rimo_surrogate_create": (C.c_int, [C.c_uint64, C.POINTER(_P)]),

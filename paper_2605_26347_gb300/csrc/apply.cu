@@ -240,6 +240,16 @@ rimo_status rimo_profile_read(rimo_plan_t p, double* ms, int64_t* launches, int3
     RIMO_API_END
 }
 
+rimo_status rimo_plan_set_wait_test(rimo_plan_t p, int32_t stall, int32_t polls) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    if (stall != 0 && stall != 1) fail(RIMO_ERR_INVALID_ARG, "stall must be 0 or 1");
+    if (stall && (polls < 1 || polls > (1 << 15))) fail(RIMO_ERR_INVALID_ARG, "polls must be in [1, 32768]");
+    p->test_stall = stall;
+    p->test_polls = stall ? (uint32_t)polls : 0u;
+    RIMO_API_END
+}
+
 rimo_status rimo_plan_status(rimo_plan_t p, void* stream) {
     RIMO_API_BEGIN
     check_plan(p);

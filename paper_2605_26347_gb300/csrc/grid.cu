@@ -56,10 +56,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: at most 2^15 suspended polls of <= 100 us (about 3 s); never spins forever.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 15); ++it)
+// Bounded wait: at most `polls` suspended polls of <= 100 us (2^15: about 3 s); never spins
+// forever.
+constexpr uint32_t WAIT_POLLS = 1u << 15;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls = WAIT_POLLS) {
+    for (uint32_t it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// The consumers' bounded wait, which also gives up once the block has abandoned the launch
+// (the producer stops issuing chunks after a failed wait of its own).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (uint32_t it = 0; it < WAIT_POLLS; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
     return false;
 }
 
@@ -97,6 +108,10 @@ struct GtgArgs {
     const uint8_t* need;    // [tile] of this bin: some footprint reaches the tile
     int ntv, shift;
     int prefetch;           // the producer bulk-copies the next unit's X patch (double buffer)
+    // failure-detection test (rimo_plan_set_wait_test): the consumers withhold their release
+    // of ring slots, and the producer's waits on the consumers give up after peer_polls
+    int stall;
+    uint32_t peer_polls;    // poll limit of the producer's waits on other warps (empty, xfree)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -295,7 +310,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 // X patch of this unit into buffer r & 1, once the consumers released it
                 // (unit r - 2); rows wrap along u, a row past the last column splits in two
                 const int j = r & 1;
-                if (r >= 2 && !s_abort && !mbar_wait_bounded(&xfree[j], ((r >> 1) - 1) & 1)) {
+                if (r >= 2 && !s_abort && !mbar_wait_bounded(&xfree[j], ((r >> 1) - 1) & 1, A.peer_polls)) {
                     s_abort = 1;
                     atomicExch(A.status, 1);
                 }
@@ -322,7 +337,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 const int64_t v0 = td.vb + (int64_t)c * GTG_CV;
                 const uint32_t nv = (uint32_t)((td.ve - v0) < GTG_CV ? (td.ve - v0) : GTG_CV);
                 const uint32_t b = g % NB, use = g / NB;
-                if (use > 0 && !s_abort && !mbar_wait_bounded(&empty[b], (use - 1) & 1)) {
+                if (use > 0 && !s_abort && !mbar_wait_bounded(&empty[b], (use - 1) & 1, A.peer_polls)) {
                     s_abort = 1;
                     atomicExch(A.status, 1);
                 }
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
         float xm = 0.f;
         float2* Xs = (r & 1) && pre ? Xbuf1 : Xbuf0;
-        if (pre && !s_abort && !mbar_wait_bounded(&xfull[r & 1], (r >> 1) & 1)) {
+        if (pre && !s_abort && !mbar_wait_or_abort(&xfull[r & 1], (r >> 1) & 1, &s_abort)) {
             s_abort = 1;
             atomicExch(A.status, 1);
         }
@@ -405,7 +420,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         }
         for (int c = 0; c < nchunks; ++c, ++g) {
             const uint32_t b = g % NB, par = (g / NB) & 1;
-            if (!s_abort && !mbar_wait_bounded(&full[b], par)) {
+            if (!s_abort && !mbar_wait_or_abort(&full[b], par, &s_abort)) {
                 s_abort = 1;
                 atomicExch(A.status, 1);
             }
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                                    mt.orig, A.y_in, A.y_out);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[b]);
+            if (lane == 0 && !A.stall) mbar_arrive(&empty[b]);
         }
         if (pre) {
             __syncwarp();
@@ -492,6 +507,8 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
     // prefetch the X patches when a double buffer still leaves a GTG_NBUF-deep tap ring
     A.prefetch = MODE != 1 && gtg_smem(p, MODE, 4, true) <= limit;
+    A.stall = p->test_stall;
+    A.peer_polls = p->test_stall ? p->test_polls : WAIT_POLLS;
     A.nbuf = GTG_NBUF;
     while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf, A.prefetch) > limit) --A.nbuf;
     const size_t sm = gtg_smem(p, MODE, A.nbuf, A.prefetch);

@@ -135,6 +135,8 @@ struct rimo_plan {
     uint32_t* d_fx = nullptr;      // fixed-point grid-step bounds (layout: rimo::FX_*)
     int max_tiles_bin = 0, chunk_vis = rimo::GTG_CHUNK, chunk_bytes = 0, nbuf = 4, n_sm = 0;
     int device = 0;                // CUDA device the plan lives on
+    int test_stall = 0;            // failure-detection test of the grid step's bounded waits
+    uint32_t test_polls = 0;       // (rimo_plan_set_wait_test)
     std::vector<int32_t> need_host;  // needed tiles of all bins (host copy of d_need_list)
     std::vector<std::vector<uint16_t>> trows;  // per bin: uv-tile rows (tu) holding a needed tile
     float2* d_kwtab = nullptr;  // tabulated folded w-kernels (wkernel_table > 0), (kw_n + 3) x 25
