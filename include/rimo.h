@@ -144,6 +144,13 @@ typedef struct rimo_plan_info {
     int32_t truncated;         /* 1: at the largest residual w the kernel needs more */
                                /* than max_wsupport taps to keep w_norm_frac         */
     int32_t weighted;          /* 1: a data weighting is injected (set_weights)    */
+    /* Holographic matrices (0 until rimo_build_holographic has run; Section 3.3): */
+    int64_t h_entries;         /* stored entries: covered owner cells x entries per  */
+                               /* owner row, each unordered pair of cells once       */
+    int64_t h_nonzero;         /* stored entries that are not zero (cell pairs that  */
+                               /* some visibility's footprint covers together)       */
+    int64_t h_nnz;             /* non-zeros of the full Hermitian H_p = G_p^H G_p,   */
+                               /* summed over bins: both triangles and the diagonal  */
 } rimo_plan_info;
 
 typedef struct rimo_plan* rimo_plan_t;
@@ -243,6 +250,17 @@ rimo_status rimo_plan_get_bins(rimo_plan_t plan, double* w_stack, int32_t* bins,
  */
 rimo_status rimo_plan_get_tiles(rimo_plan_t plan, const int64_t* idx, int64_t n, int32_t* g0,
                                 int32_t* h0, int32_t* S, rimo_cfloat* taps, void* stream);
+
+/*
+ * The image-domain factor Z_p of w-bin `bin` (Eq. 6: grid correction times the w-layer
+ * chirp e^{-2 pi i w_stack[bin] (sqrt(1 - l^2 - m^2) - 1)} of Eq. 2, divided by
+ * sqrt(1 - l^2 - m^2) with n_weight = DIV_N), exactly as the transform kernels evaluate it
+ * (the w-phase argument and its range reduction in double-float arithmetic, then one
+ * single-precision sincos).  out_dev: device, ny x nx complex, row-major, pixel (i, j) at
+ * l = (j - nx/2) fov_x / nx, m = (i - ny/2) fov_y / ny; enqueued on `stream`.
+ * Errors: INVALID_ARG (null plan or buffer, bin out of range), CUDA.
+ */
+rimo_status rimo_plan_get_zlayer(rimo_plan_t plan, int32_t bin, rimo_cfloat* out_dev, void* stream);
 
 /*
  * y = Phi x (Eq. 6).  x_dev: device, ny x nx image; y_dev: device, M visibilities in

@@ -186,6 +186,13 @@ class Plan:
         non-finite input (INVALID_ARG) since the last check (rimo_plan_status)."""
         _lib.check(self._lib.rimo_plan_status(self._h, _stream_ptr(stream)))
 
+    def zlayer(self, bin: int, stream=None):
+        """Z_p of w-bin `bin` at every pixel as the kernels evaluate it (rimo_plan_get_zlayer)."""
+        torch = _torch()
+        out = torch.empty((self.ny, self.nx), dtype=torch.complex64, device="cuda")
+        _lib.check(self._lib.rimo_plan_get_zlayer(self._h, int(bin), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
     def set_wait_test(self, stall: bool, polls: int = 16) -> None:
         """Failure-detection test of the grid step's bounded waits (rimo_plan_set_wait_test)."""
         _lib.check(self._lib.rimo_plan_set_wait_test(self._h, int(bool(stall)), int(polls)))

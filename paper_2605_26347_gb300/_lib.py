@@ -69,6 +69,9 @@ class PlanInfo(C.Structure):
         ("tile_size", C.c_int32),
         ("truncated", C.c_int32),
         ("weighted", C.c_int32),
+        ("h_entries", C.c_int64),
+        ("h_nonzero", C.c_int64),
+        ("h_nnz", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -96,6 +99,7 @@ _PROTOS = {
     "rimo_psf": (C.c_int, [_P, _P, _P]),
     "rimo_plan_status": (C.c_int, [_P, _P]),
     "rimo_plan_set_wait_test": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "rimo_plan_get_zlayer": (C.c_int, [_P, C.c_int32, _P, _P]),
     "rimo_profile_enable": (C.c_int, [_P, C.c_int32]),
     "rimo_profile_read": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
     "rimo_surrogate_create": (C.c_int, [C.c_uint64, C.POINTER(_P)]),

@@ -240,6 +240,16 @@ rimo_status rimo_profile_read(rimo_plan_t p, double* ms, int64_t* launches, int3
     RIMO_API_END
 }
 
+rimo_status rimo_plan_get_zlayer(rimo_plan_t p, int32_t bin, rimo_cfloat* out, void* stream) {
+    RIMO_API_BEGIN
+    check_plan(p);
+    if (!out) fail(RIMO_ERR_INVALID_ARG, "null buffer");
+    if (bin < 0 || bin >= p->P) fail(RIMO_ERR_INVALID_ARG, "bin out of range");
+    launch_zlayer(p, bin, (float2*)out, (cudaStream_t)stream);
+    RIMO_CUDA(cudaGetLastError());
+    RIMO_API_END
+}
+
 rimo_status rimo_plan_set_wait_test(rimo_plan_t p, int32_t stall, int32_t polls) {
     RIMO_API_BEGIN
     check_plan(p);

@@ -580,6 +580,16 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
     }
 }
 
+// ----------------------------------------------------------------------------- Z_p
+// Z_p(i, j) of every pixel, as the row passes apply it (for checking the w-phase).
+__global__ void __launch_bounds__(256) zlayer_kernel(ZArgs z, int nx, int ny, float2* __restrict__ out) {
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nx), j = (int)(e - (int64_t)i * nx);
+        out[e] = z_factor(z, i, j, i - ny / 2, j - nx / 2);
+    }
+}
+
 // ----------------------------------------------------------------------------- launchers
 static ZArgs zargs(const rimo_plan* p, int bin) {
     ZArgs z;
@@ -588,6 +598,12 @@ static ZArgs zargs(const rimo_plan* p, int bin) {
     z.w_hi = p->bins[bin].w_hi;
     z.w_lo = p->bins[bin].w_lo;
     return z;
+}
+
+void launch_zlayer(const rimo_plan* p, int bin, float2* out, cudaStream_t s) {
+    const int64_t n = (int64_t)p->nx * p->ny;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)p->n_sm);
+    zlayer_kernel<<<blocks, 256, 0, s>>>(zargs(p, bin), p->nx, p->ny, out);
 }
 
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s) {

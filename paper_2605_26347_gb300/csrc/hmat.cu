@@ -437,6 +437,28 @@ struct DevBuf {
     ~DevBuf() { cudaFree(p); }
 };
 
+// Non-zero stored entries of a bin's owner rows: counts[0] += all, counts[1] += the
+// diagonal ones (entry 0 of a row is H[o][o]).
+__global__ void __launch_bounds__(256) hcount_kernel(const float2* __restrict__ rows, int64_t n, int ne,
+                                                     unsigned long long* counts) {
+    unsigned long long nz = 0, nd = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 h = rows[e];
+        const bool on = h.x != 0.f || h.y != 0.f;
+        nz += on;
+        nd += on && (e % ne) == 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts, nz);
+        atomicAdd(counts + 1, nd);
+    }
+}
+
 }  // namespace
 
 void launch_happly(const rimo_plan* p, int bin, cudaStream_t s) {
@@ -603,6 +625,31 @@ static void build_holographic(rimo_plan* p, cudaStream_t s) {
         RIMO_CUDA(cudaGetLastError());
     }
     RIMO_CUDA(cudaStreamSynchronize(s));
+    {
+        // fill of the stored rows: how many entries the footprints actually couple
+        unsigned long long* cnt = nullptr;
+        RIMO_CUDA(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
+        unsigned long long h[2] = {0, 0};
+        try {
+            RIMO_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+            for (int b = 0; b < P; ++b) {
+                const int nneed = p->bins[b].n1 - p->bins[b].n0;
+                const int64_t n = p->hoff_host[b][(size_t)nneed] * ne;
+                if (n == 0) continue;
+                const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)p->n_sm);
+                hcount_kernel<<<blocks, 256, 0, s>>>(p->d_hrows[b], n, ne, cnt);
+            }
+            RIMO_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+            RIMO_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaFree(cnt);
+            throw;
+        }
+        cudaFree(cnt);
+        p->info.h_entries = total * ne;
+        p->info.h_nonzero = (int64_t)h[0];
+        p->info.h_nnz = 2 * (int64_t)(h[0] - h[1]) + (int64_t)h[1];
+    }
     p->h_ne = ne;
     p->info.h_bytes = h_bytes + (int64_t)patch_bytes;
     p->h_built = true;

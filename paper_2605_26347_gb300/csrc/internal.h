@@ -251,6 +251,8 @@ void apply_phi_adj_phi_bins(rimo_plan* p, const float2* x, float2* out, int real
 // bound on the grid-step contributions of Phi^dagger Phi x (from the image x) or of
 // Phi^dagger y (from y), written to d_fx[FX_MAXTERM]; non-finite input sets status 3
 void launch_image_bound(const rimo_plan* p, const float2* x, cudaStream_t s);
+// Z_p of bin `bin` at every pixel into out (ny x nx)
+void launch_zlayer(const rimo_plan* p, int bin, float2* out, cudaStream_t s);
 void launch_y_bound(const rimo_plan* p, const float2* y, cudaStream_t s);
 // Kernel surrogate: fill d_sur_taps with the MLP's tiles of bin `bin` (and the tap bounds
 // of the fixed-point grid step); reset_surrogate_bounds clears those bounds for an apply.

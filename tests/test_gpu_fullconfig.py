@@ -108,6 +108,29 @@ def test_c5_subset_phi_adj_phi_every_pixel(c5sub):
     assert rel(zb, ref) < TOL
 
 
+def test_c5_w_phase_at_the_largest_w_stack(c5sub):
+    """Z_p element by element against the oracle's FP64 Z_p at the bin of largest |w_stack|
+    (there the w-phase w (sqrt(1 - l^2 - m^2) - 1) spans tens of turns).  An FP32 product
+    w (n - 1) before the sincos would be off by up to about |w (n - 1)| 2^-24 turns: the test
+    checks that this reading fails the bound the device's double-float phase meets."""
+    from oracle import wterm
+    plan, op = c5sub["plan"], c5sub["op"]
+    ws, _, _ = plan.bins()
+    p = int(np.argmax(np.abs(ws)))
+    zg = to_host(plan.zlayer(p))
+    zo = op.z_layer(p)
+    err = np.max(np.abs(zg - zo) / np.abs(zo))
+    assert err < 1e-6, err
+    # the same factor with the phase argument rounded to FP32 first
+    pp = op.pp
+    l = wterm.pixel_lm(pp.nx, pp.fov_x)[None, :]
+    m = wterm.pixel_lm(pp.ny, pp.fov_y)[:, None]
+    arg32 = (np.float32(ws[p]) * wterm.dn(l, m).astype(np.float32)).astype(np.float64)
+    z32 = op.gc * np.exp(-2j * math.pi * arg32)
+    assert abs(float(np.max(np.abs(op.plan.w_stack))) - abs(ws[p])) < 1e-6 * abs(ws[p])
+    assert np.max(np.abs(z32 - zo) / np.abs(zo)) > 3 * err
+
+
 def test_c3_subset_through_h_and_g():
     import paper_2605_26347_gb300 as pkg
     uvw20 = synth.make_uvw(20_000_000, 28_800, 1.28e9, seed=1003)

@@ -45,6 +45,19 @@ def test_entries_match_oracle_and_are_hermitian(holo):
     assert plan.holographic_entries(0, [[0, 0, 100, 100]])[0] == 0
 
 
+def test_nonzero_count_matches_oracle(holo):
+    # the full H_p = G_p^H G_p of the oracle, both triangles: its non-zeros over all bins
+    w, plan, op, _ = holo
+    nnz = 0
+    for p in range(op.plan.P):
+        H = op.holographic(p)
+        H.eliminate_zeros()
+        nnz += H.nnz
+    info = plan.info()
+    assert info["h_nnz"] == nnz
+    assert 0 < info["h_nonzero"] <= info["h_entries"]
+
+
 def test_phi_adj_phi_and_psf_through_h(holo):
     w, plan, op, before = holo
     out = to_host(plan.phi_adj_phi(to_dev(w.sky)))
