@@ -97,6 +97,15 @@ typedef enum rimo_n_weight {
  *                     plan and interpolated by cubic Lagrange polynomials in w_r when tiles
  *                     are built or generated (n >= 16; 8192 keeps the interpolation error
  *                     near 1e-8 relative at the 4096^2 / 50M workload).
+ *   uv_order          order of the visibilities within a uv-tile, which sets the groups of
+ *                     GTG_CHUNK (20) visibilities the grid step de-grids and grids at once
+ *                     (a scheduling choice of this design, no counterpart in the paper):
+ *                     0 = time-interleaved (the tile's list in time order read as 20 rows,
+ *                     column by column: a group's visibilities come from far-apart instants
+ *                     and rarely update the same grid cells; default), 1 = time order,
+ *                     2 = shuffled by a counter-based SplitMix64 hash of the visibility
+ *                     index.  Results agree within rounding (the grid step sums exactly
+ *                     in fixed point; only the split of heavy tiles into units moves).
  */
 typedef struct rimo_plan_params {
     int32_t nx, ny;
@@ -118,6 +127,7 @@ typedef struct rimo_plan_params {
     int32_t tile_size;
     int64_t block_bytes_max;
     int32_t wkernel_table;
+    int32_t uv_order;
 } rimo_plan_params;
 
 /* Results of planning (stage 1 of Fig. 3) and the state of a plan. */
@@ -452,24 +462,52 @@ rimo_status rimo_surrogate_train_step(rimo_surrogate_t s, const float* x_dev, co
  */
 typedef struct rimo_batch* rimo_batch_t;
 /* Errors: INVALID_ARG (no plans, NULL plan, a plan twice, image sizes differ, plans on
- * another device), CUDA. */
+ * another device), OOM (staged scratch), CUDA.  Same as rimo_batch_create_form with
+ * RIMO_BATCH_AUTO. */
 rimo_status rimo_batch_create(const rimo_plan_t* plans, int32_t n_plans, rimo_batch_t* out);
+/*
+ * The form of a batch's recorded Phi^dagger Phi:
+ *  RIMO_BATCH_STAGED   every (channel, w-bin) of the batch is a job with scratch of its own
+ *                      (2 nx ny + 4 nx ny complex64 plus its tile patches, allocated once
+ *                      here, freed by rimo_batch_destroy; rimo_batch_layout reports the
+ *                      bytes), and each pass of Eq. 7-8 is ONE launch over all jobs: forward
+ *                      rows and cols (F Z_p), the grid step G_p^H G_p as one persistent
+ *                      launch whose blocks take the work units (uv-tiles or slices of heavy
+ *                      ones) of every channel and bin from one heaviest-first queue, the
+ *                      merge of split tiles, the fold, inverse cols, and inverse rows that
+ *                      also sums each channel's bins.  Needs stored-G plans (no H) with
+ *                      square images of one size (64 .. 4096) and one uv-tile size.
+ *  RIMO_BATCH_BRANCHES each channel's own apply on a branch of a fork/join pattern.
+ *  RIMO_BATCH_AUTO     staged when the plans allow it, else branches.
+ * Results are the same in both forms, bit for bit (fixed-point grid step, same kernels).
+ * Errors: as rimo_batch_create; UNSUPPORTED (STAGED asked for plans that do not allow it).
+ */
+#define RIMO_BATCH_AUTO 0
+#define RIMO_BATCH_STAGED 1
+#define RIMO_BATCH_BRANCHES 2
+rimo_status rimo_batch_create_form(const rimo_plan_t* plans, int32_t n_plans, int32_t form, rimo_batch_t* out);
 /* NULL is accepted. */
 rimo_status rimo_batch_destroy(rimo_batch_t batch);
 /*
  * out[c] = Phi_c^dagger Phi_c x[c] for every channel c of the batch, where x_dev and
  * out_dev hold n_plans images of ny x nx complex64 back to back (device, distinct,
  * non-overlapping).  The first call, and any call with other buffers or another
- * real_part_only, records every channel's apply into one CUDA graph (each channel on its
- * own forked branch of `stream`, so channels run concurrently); each call then enqueues
- * that graph with a single launch on `stream`.  Per-plan stage timers are not recorded
- * inside the graph.  Device-side error flags are per plan (rimo_plan_status).
+ * real_part_only, records the batch's form (see rimo_batch_create_form) into one CUDA
+ * graph, after waiting for the device to finish earlier work (a staged batch rewrites
+ * its job tables); each call then enqueues that graph with a single launch on `stream`.
+ * Per-plan stage timers are not recorded inside the graph.  Device-side error flags are
+ * per plan (rimo_plan_status).
  * Errors: INVALID_ARG, CUDA.
  */
 rimo_status rimo_batch_apply_phi_adj_phi(rimo_batch_t batch, const rimo_cfloat* x_dev, rimo_cfloat* out_dev,
                                          int32_t real_part_only, void* stream);
 /* Number of plans and how many times the graph was recorded (either may be NULL). */
 rimo_status rimo_batch_info(rimo_batch_t batch, int32_t* n_plans, int64_t* captures);
+/* The batch's form and work (any pointer may be NULL): staged (1) or branches (0); the
+ * (channel, w-bin) jobs and the grid-step work units of the staged form; the bytes of its
+ * job scratch. */
+rimo_status rimo_batch_layout(rimo_batch_t batch, int32_t* staged, int64_t* jobs, int64_t* units,
+                              int64_t* scratch_bytes);
 
 /*
  * Tile-size autotuner (no counterpart in the paper: a scheduling choice of this design).
@@ -484,6 +522,16 @@ rimo_status rimo_batch_info(rimo_batch_t batch, int32_t* n_plans, int64_t* captu
  */
 rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
                                void* stream, int32_t* tile_out, double* ms_out);
+/*
+ * The same over both scheduling choices of the grid step: uv-tile size (32, 64) and the
+ * order of visibilities within a tile (uv_order 0, 1, 2; see rimo_plan_params), six plans
+ * timed on the subsample in the order (32, 0), (32, 1), (32, 2), (64, 0), (64, 1), (64, 2).
+ * Writes the fastest to *tile_out and *order_out; ms_out (host, 6 values, may be NULL):
+ * their ms per apply, or -1 when not timed.  Cache entries (key suffix "_tile_order")
+ * hold tile * 10 + order.  Errors as rimo_autotune_tile.
+ */
+rimo_status rimo_autotune(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
+                          void* stream, int32_t* tile_out, int32_t* order_out, double* ms_out);
 
 /*
  * Data weighting injected into the measurement operator (Section 2, Eq. 3: a weighting

@@ -322,13 +322,19 @@ class Surrogate:
         _lib.check(self._lib.rimo_surrogate_set_w_scale(self._h, float(value)))
 
 
+BATCH_AUTO, BATCH_STAGED, BATCH_BRANCHES = 0, 1, 2
+
+
 class Batch:
     """Batched wideband Phi^dagger Phi over per-channel plans (rimo_batch_create).
 
     Keeps references to the plans; they must outlive the batch and share one image size.
+    form: BATCH_AUTO (staged when the plans allow it), BATCH_STAGED (one launch per pass over
+    every (channel, w-bin), the grid step one persistent launch over all their work units)
+    or BATCH_BRANCHES (each channel's apply on its own graph branch).
     """
 
-    def __init__(self, plans):
+    def __init__(self, plans, form: int = 0):
         self._lib = _lib.load()
         self.plans = list(plans)
         if not self.plans:
@@ -336,7 +342,7 @@ class Batch:
         self.nx, self.ny = self.plans[0].nx, self.plans[0].ny
         arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
         h = C.c_void_p()
-        _lib.check(self._lib.rimo_batch_create(arr, len(self.plans), C.byref(h)))
+        _lib.check(self._lib.rimo_batch_create_form(arr, len(self.plans), int(form), C.byref(h)))
         self._h = h
 
     def close(self):
@@ -369,6 +375,12 @@ class Batch:
         caps = C.c_int64()
         _lib.check(self._lib.rimo_batch_info(self._h, C.byref(n), C.byref(caps)))
         return {"n_plans": n.value, "captures": caps.value}
+
+    def layout(self) -> dict:
+        st = C.c_int32()
+        jobs, units, sb = C.c_int64(), C.c_int64(), C.c_int64()
+        _lib.check(self._lib.rimo_batch_layout(self._h, C.byref(st), C.byref(jobs), C.byref(units), C.byref(sb)))
+        return {"staged": bool(st.value), "jobs": jobs.value, "units": units.value, "scratch_bytes": sb.value}
 
 
 def fb_step(x, g, dirty, gamma: float, out=None, stream=None):
@@ -442,6 +454,18 @@ def autotune_tile(uvw, params: PlanParams, cache_path: str | None = None, stream
     _lib.check(lib.rimo_autotune_tile(u.ctypes.data, u.shape[0], C.byref(params), path, _stream_ptr(stream),
                                       C.byref(tile), ms))
     return tile.value, [ms[0], ms[1]]
+
+
+def autotune(uvw, params: PlanParams, cache_path: str | None = None, stream=None) -> dict:
+    """rimo_autotune: the fastest uv-tile size and visibility order, with the six timings."""
+    lib = _lib.load()
+    u = _uvw_arg(uvw)
+    tile, order = C.c_int32(), C.c_int32()
+    ms = (C.c_double * 6)()
+    path = cache_path.encode() if cache_path else None
+    _lib.check(lib.rimo_autotune(u.ctypes.data, u.shape[0], C.byref(params), path, _stream_ptr(stream),
+                                 C.byref(tile), C.byref(order), ms))
+    return {"tile_size": tile.value, "uv_order": order.value, "ms": list(ms)}
 
 
 def unpack_params(p: np.ndarray) -> dict:

@@ -43,6 +43,7 @@ class PlanParams(C.Structure):
         ("tile_size", C.c_int32),
         ("block_bytes_max", C.c_int64),
         ("wkernel_table", C.c_int32),
+        ("uv_order", C.c_int32),
     ]
 
 
@@ -113,7 +114,10 @@ _PROTOS = {
     "rimo_batch_destroy": (C.c_int, [_P]),
     "rimo_batch_apply_phi_adj_phi": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "rimo_batch_info": (C.c_int, [_P, _P, _P]),
+    "rimo_batch_create_form": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(_P)]),
+    "rimo_batch_layout": (C.c_int, [_P, _P, _P, _P, _P]),
     "rimo_autotune_tile": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P]),
+    "rimo_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P, _P]),
     "rimo_plan_set_surrogate": (C.c_int, [_P, _P]),
     "rimo_surrogate_fit": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P, _P]),
     "rimo_surrogate_get_w_scale": (C.c_int, [_P, C.POINTER(C.c_float)]),

@@ -2,17 +2,23 @@
 //
 // A batch groups independent plans (one per frequency channel, each with its own w-stack,
 // Section 2 and Section 3.5: the wideband model applies the monochromatic one per
-// channel).  One call enqueues every channel's Phi^dagger Phi on its own branch of a
-// fork/join stream pattern inside a single stream capture; the instantiated CUDA graph is
-// then replayed by one cudaGraphLaunch per call for as long as the buffers stay the same.
-// Channels share no state, so the branches run concurrently and the small per-channel
-// kernels fill the GPU together.
+// channel).  Its Phi^dagger Phi is recorded once into a CUDA graph and replayed by one
+// cudaGraphLaunch per call for as long as the buffers stay the same, in one of two forms:
+//  * staged (plans with stored G and one image, uv-tile, patch and tap-ring shape): every
+//    (channel, w-bin) is a job with its own scratch, and each pass runs as ONE launch over
+//    all jobs - forward rows, forward cols, the grid step as one persistent launch that
+//    takes the work units of every job heaviest first from one queue (channels and bins of
+//    uneven visibility counts balance across the SMs), the merge of split tiles, the fold,
+//    inverse cols, and inverse rows with the sum over each channel's bins;
+//  * branches (any other batch): each channel's own apply on a branch of a fork/join
+//    stream pattern, the branches running concurrently.
 //
 // The autotuner times the uv-tile size candidates of a plan (the tile shape drives the
 // gridding schedule: patch halo overhead against work-unit count) on a deterministic
 // subsample of the visibilities and keeps the winner in a JSON cache keyed by the
 // workload's shape.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <fstream>
@@ -38,6 +44,14 @@ struct rimo_batch {
     void* key_out = nullptr;
     int key_real = -1;
     int64_t captures = 0;
+    // staged form
+    bool staged = false;
+    std::vector<WideJob> jobs;          // (channel, w-bin) jobs, channel-major
+    std::vector<bool> has_jobs;         // per channel: some bin holds visibilities
+    void* scratch = nullptr;            // every job's scratch, one allocation
+    int64_t scratch_bytes = 0;
+    WideGtg* wgtg = nullptr;
+    WideFft* wfft = nullptr;            // tables for the recorded (x, out)
 };
 
 namespace {
@@ -50,6 +64,9 @@ void destroy_batch(rimo_batch* b) {
     cudaGetDevice(&cur);
     cudaSetDevice(b->device);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->wfft) wide_fft_destroy(b->wfft);
+    if (b->wgtg) wide_gtg_destroy(b->wgtg);
+    if (b->scratch) cudaFree(b->scratch);
     for (auto e : b->joins) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     for (auto s : b->branches) cudaStreamDestroy(s);
@@ -58,9 +75,68 @@ void destroy_batch(rimo_batch* b) {
     delete b;
 }
 
-// Records all channels' applies into a graph on the batch's own root stream: fork, one
-// branch stream per channel (round robin over the branch pool), join back.  Nothing runs
-// during recording; the graph is launched on the caller's stream afterwards.
+// Whether the plans can run as one staged pipeline: stored G (no H, no generated tiles),
+// square images of one size and one uv-tile size (patch sides and tap chunks may differ).
+bool stage_eligible(const std::vector<rimo_plan*>& plans) {
+    const rimo_plan* a = plans[0];
+    for (const rimo_plan* p : plans) {
+        if (p->mode != RIMO_MODE_STORED_G || p->h_built) return false;
+        if (p->nx != p->ny || p->nx != a->nx || p->TS != a->TS || p->nx > 4096 || p->nx < 64) return false;
+    }
+    return true;
+}
+
+// Jobs, their scratch (one allocation, 256-byte aligned parts) and the grid-step queue.
+void stage(rimo_batch* b, cudaStream_t s) {
+    auto al = [](int64_t x) { return (x + 255) & ~(int64_t)255; };
+    int64_t total = 0;
+    std::vector<std::array<int64_t, 3>> off;
+    b->has_jobs.assign(b->plans.size(), false);
+    for (size_t c = 0; c < b->plans.size(); ++c) {
+        const rimo_plan* p = b->plans[c];
+        for (int bin = 0; bin < p->P; ++bin) {
+            if (p->bins[bin].ve == p->bins[bin].vb) continue;
+            const int64_t ab = al((int64_t)2 * p->nx * p->ny * 8), gx = al((int64_t)p->gx * p->gy * 8);
+            const int64_t pt = al((int64_t)std::max(1, p->bins[bin].t1 - p->bins[bin].t0) * p->PW * p->PW * 8);
+            off.push_back({total, total + ab, total + ab + gx});
+            total += ab + gx + pt;
+            b->jobs.push_back(WideJob{p, bin, (int)c, nullptr, nullptr, nullptr});
+            b->has_jobs[c] = true;
+        }
+    }
+    if (b->jobs.empty()) return;
+    if (cudaMalloc(&b->scratch, (size_t)total) != cudaSuccess) {
+        cudaGetLastError();
+        fail(RIMO_ERR_OOM, "batch scratch of " + std::to_string(total) + " bytes");
+    }
+    b->scratch_bytes = total;
+    char* base = static_cast<char*>(b->scratch);
+    for (size_t j = 0; j < b->jobs.size(); ++j) {
+        b->jobs[j].AB = reinterpret_cast<float2*>(base + off[j][0]);
+        b->jobs[j].X = reinterpret_cast<float2*>(base + off[j][1]);
+        b->jobs[j].patch = reinterpret_cast<float2*>(base + off[j][2]);
+    }
+    b->wgtg = wide_gtg_create(b->jobs, s);
+}
+
+// Records the staged pipeline for (x, out): per channel the image bound (flags non-finite
+// input in the plan's status), then one launch per pass over all jobs.
+void record_staged(rimo_batch* b, const float2* x, float2* out, int real_only, cudaStream_t s) {
+    const size_t img = (size_t)b->nx * b->ny;
+    for (size_t c = 0; c < b->plans.size(); ++c) {
+        if (b->has_jobs[c]) launch_image_bound(b->plans[c], x + c * img, s);
+        else RIMO_CUDA(cudaMemsetAsync(out + c * img, 0, img * sizeof(float2), s));
+    }
+    if (b->jobs.empty()) return;
+    wide_fwd(b->wfft, s);
+    wide_gtg(b->wgtg, s);
+    wide_inv(b->wfft, real_only, s);
+}
+
+// Records all channels' applies into a graph on the batch's own root stream (staged: one
+// launch per pass; branches: fork, one branch stream per channel round robin over the
+// branch pool, join back).  Nothing runs during recording; the graph is launched on the
+// caller's stream afterwards.
 void capture(rimo_batch* b, const float2* x, float2* out, int real_only) {
     cudaStream_t s = b->root;
     const size_t img = (size_t)b->nx * b->ny;
@@ -69,16 +145,33 @@ void capture(rimo_batch* b, const float2* x, float2* out, int real_only) {
         prof[i] = b->plans[i]->prof_on;
         b->plans[i]->prof_on = false;  // stage timers record events the graph cannot replay
     }
+    if (b->staged && !b->jobs.empty()) {
+        // the job tables point at (x, out); a graph of the previous tables may still run
+        RIMO_CUDA(cudaDeviceSynchronize());
+        if (b->wfft) wide_fft_destroy(b->wfft);
+        b->wfft = nullptr;
+        std::vector<const float2*> xs;
+        std::vector<float2*> os;
+        for (size_t c = 0; c < b->plans.size(); ++c) {
+            xs.push_back(x + c * img);
+            os.push_back(out + c * img);
+        }
+        b->wfft = wide_fft_create(b->jobs, xs, os, s);
+    }
     RIMO_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaGraph_t graph = nullptr;
     try {
-        RIMO_CUDA(cudaEventRecord(b->fork, s));
-        for (size_t i = 0; i < b->plans.size(); ++i) {
-            cudaStream_t br = b->branches[i % b->branches.size()];
-            RIMO_CUDA(cudaStreamWaitEvent(br, b->fork, 0));
-            apply_phi_adj_phi(b->plans[i], x + i * img, out + i * img, real_only, br);
-            RIMO_CUDA(cudaEventRecord(b->joins[i], br));
-            RIMO_CUDA(cudaStreamWaitEvent(s, b->joins[i], 0));
+        if (b->staged) {
+            record_staged(b, x, out, real_only, s);
+        } else {
+            RIMO_CUDA(cudaEventRecord(b->fork, s));
+            for (size_t i = 0; i < b->plans.size(); ++i) {
+                cudaStream_t br = b->branches[i % b->branches.size()];
+                RIMO_CUDA(cudaStreamWaitEvent(br, b->fork, 0));
+                apply_phi_adj_phi(b->plans[i], x + i * img, out + i * img, real_only, br);
+                RIMO_CUDA(cudaEventRecord(b->joins[i], br));
+                RIMO_CUDA(cudaStreamWaitEvent(s, b->joins[i], 0));
+            }
         }
         RIMO_CUDA(cudaStreamEndCapture(s, &graph));
     } catch (...) {
@@ -153,10 +246,16 @@ std::string tune_key(const rimo_plan_params& q, int64_t M, int P, int max_s) {
 extern "C" {
 
 rimo_status rimo_batch_create(const rimo_plan_t* plans, int32_t n_plans, rimo_batch_t* out) {
+    return rimo_batch_create_form(plans, n_plans, RIMO_BATCH_AUTO, out);
+}
+
+rimo_status rimo_batch_create_form(const rimo_plan_t* plans, int32_t n_plans, int32_t form, rimo_batch_t* out) {
     if (out) *out = nullptr;
     rimo_batch* b = nullptr;
     RIMO_API_BEGIN
     if (!out || !plans || n_plans <= 0) fail(RIMO_ERR_INVALID_ARG, "need an output and at least one plan");
+    if (form != RIMO_BATCH_AUTO && form != RIMO_BATCH_STAGED && form != RIMO_BATCH_BRANCHES)
+        fail(RIMO_ERR_INVALID_ARG, "unknown batch form");
     b = new rimo_batch();
     RIMO_CUDA(cudaGetDevice(&b->device));
     for (int i = 0; i < n_plans; ++i) {
@@ -173,7 +272,12 @@ rimo_status rimo_batch_create(const rimo_plan_t* plans, int32_t n_plans, rimo_ba
             if (plans[j] == p) fail(RIMO_ERR_INVALID_ARG, "a plan appears twice in the batch (it has scratch)");
         b->plans.push_back(p);
     }
+    const bool eligible = stage_eligible(b->plans);
+    if (form == RIMO_BATCH_STAGED && !eligible)
+        fail(RIMO_ERR_UNSUPPORTED, "staged batches need stored-G plans of one image, tile, patch and ring shape");
+    b->staged = form != RIMO_BATCH_BRANCHES && eligible;
     RIMO_CUDA(cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking));
+    if (b->staged) stage(b, b->root);
     const int nb = std::min(n_plans, BATCH_MAX_BRANCHES);
     for (int i = 0; i < nb; ++i) {
         cudaStream_t st = nullptr;
@@ -236,13 +340,26 @@ rimo_status rimo_batch_info(rimo_batch_t b, int32_t* n_plans, int64_t* captures)
     RIMO_API_END
 }
 
-rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
-                               void* stream, int32_t* tile_out, double* ms_out) {
+rimo_status rimo_batch_layout(rimo_batch_t b, int32_t* staged, int64_t* jobs, int64_t* units,
+                              int64_t* scratch_bytes) {
     RIMO_API_BEGIN
-    if (!uvw || M <= 0 || !base || !tile_out) fail(RIMO_ERR_INVALID_ARG, "null argument or empty data");
-    const int cands[2] = {32, 64};
-    if (ms_out) ms_out[0] = ms_out[1] = -1.0;
-    // deterministic subsample: every stride-th row, at most 1M rows
+    if (!b) fail(RIMO_ERR_INVALID_ARG, "null batch");
+    if (staged) *staged = b->staged ? 1 : 0;
+    if (jobs) *jobs = (int64_t)b->jobs.size();
+    if (units) *units = b->wgtg ? wide_gtg_units(b->wgtg) : 0;
+    if (scratch_bytes) *scratch_bytes = b->scratch_bytes;
+    RIMO_API_END
+}
+
+}  // extern "C"
+
+namespace {
+
+// Times Phi^dagger Phi for each candidate (uv-tile size, visibility order) on plans built
+// from a deterministic subsample (every stride-th row, at most 2^20 rows) and returns the
+// index of the fastest; ms[c] receives each candidate's ms per apply.
+int tune(const double* uvw, int64_t M, const rimo_plan_params* base, const std::vector<std::pair<int, int>>& cands,
+         void* stream, double* ms) {
     const int64_t cap = 1 << 20;
     const int64_t stride = (M + cap - 1) / cap;
     std::vector<double> sub;
@@ -256,12 +373,82 @@ rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_par
         src = sub.data();
     }
     rimo_plan_params q = *base;
+    cudaStream_t s = (cudaStream_t)stream;
+    float2 *x = nullptr, *o = nullptr;
+    const size_t img = (size_t)q.nx * q.ny * sizeof(float2);
+    RIMO_CUDA(cudaMalloc(&x, img));
+    RIMO_CUDA(cudaMalloc(&o, img));
+    double best = 1e300;
+    int pick = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        // a point at the centre and one off-centre: every bin's grid is non-trivial
+        RIMO_CUDA(cudaMemsetAsync(x, 0, img, s));
+        const float2 one = make_float2(1.f, 0.f);
+        RIMO_CUDA(cudaMemcpyAsync(x + (size_t)(q.ny / 2) * q.nx + q.nx / 2, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaMemcpyAsync(x + (size_t)(q.ny / 4) * q.nx + q.nx / 3, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaEventCreate(&e0));
+        RIMO_CUDA(cudaEventCreate(&e1));
+        for (size_t c = 0; c < cands.size(); ++c) {
+            q.tile_size = cands[c].first;
+            q.uv_order = cands[c].second;
+            rimo_plan_t p = nullptr;
+            if (rimo_plan_create(src, Ms, &q, stream, &p) != RIMO_OK) fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
+            float t = 0.f;
+            try {
+                apply_phi_adj_phi(p, x, o, 0, s);  // warm-up
+                RIMO_CUDA(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) apply_phi_adj_phi(p, x, o, 0, s);
+                RIMO_CUDA(cudaEventRecord(e1, s));
+                RIMO_CUDA(cudaEventSynchronize(e1));
+                RIMO_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            } catch (...) {
+                rimo_plan_destroy(p);
+                throw;
+            }
+            rimo_plan_destroy(p);
+            ms[c] = t / 3.0;
+            if (ms[c] < best) {
+                best = ms[c];
+                pick = (int)c;
+            }
+        }
+    } catch (...) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(x);
+        cudaFree(o);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(o);
+    return pick;
+}
+
+// cache key of a workload's shape (image, FoV, log2 M, P, J, largest tile side), from a
+// host-only estimate on the same subsample the tuner times
+std::string shape_key(const double* uvw, int64_t M, const rimo_plan_params* base, const char* suffix) {
+    rimo_plan_params q = *base;
     q.tile_size = 0;
     rimo_plan_info est;
-    if (rimo_plan_estimate(src, Ms, &q, &est) != RIMO_OK) fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
+    if (rimo_plan_estimate(uvw, M, &q, &est) != RIMO_OK) fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
     int max_s = 0;
     for (int i = 0; i < 64; ++i) max_s = std::max(max_s, (int)est.support_table[i]);
-    const std::string key = tune_key(q, M, est.P, max_s + q.kb_support - 1);
+    return tune_key(q, M, est.P, max_s + q.kb_support - 1) + suffix;
+}
+
+}  // namespace
+
+extern "C" {
+
+rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
+                               void* stream, int32_t* tile_out, double* ms_out) {
+    RIMO_API_BEGIN
+    if (!uvw || M <= 0 || !base || !tile_out) fail(RIMO_ERR_INVALID_ARG, "null argument or empty data");
+    if (ms_out) ms_out[0] = ms_out[1] = -1.0;
+    const std::string key = shape_key(uvw, M, base, "");
     std::map<std::string, int> cache;
     if (cache_path && *cache_path) {
         cache = read_cache(cache_path);
@@ -271,58 +458,46 @@ rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_par
             return RIMO_OK;
         }
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    float2 *x = nullptr, *o = nullptr;
-    const size_t img = (size_t)q.nx * q.ny * sizeof(float2);
-    RIMO_CUDA(cudaMalloc(&x, img));
-    RIMO_CUDA(cudaMalloc(&o, img));
-    double best = 1e300;
-    int pick = cands[0];
-    try {
-        // a point at the centre and one off-centre: every bin's grid is non-trivial
-        RIMO_CUDA(cudaMemsetAsync(x, 0, img, s));
-        const float2 one = make_float2(1.f, 0.f);
-        RIMO_CUDA(cudaMemcpyAsync(x + (size_t)(q.ny / 2) * q.nx + q.nx / 2, &one, sizeof(one), cudaMemcpyHostToDevice, s));
-        RIMO_CUDA(cudaMemcpyAsync(x + (size_t)(q.ny / 4) * q.nx + q.nx / 3, &one, sizeof(one), cudaMemcpyHostToDevice, s));
-        cudaEvent_t e0, e1;
-        RIMO_CUDA(cudaEventCreate(&e0));
-        RIMO_CUDA(cudaEventCreate(&e1));
-        for (int c = 0; c < 2; ++c) {
-            q.tile_size = cands[c];
-            rimo_plan_t p = nullptr;
-            if (rimo_plan_create(src, Ms, &q, stream, &p) != RIMO_OK) fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
-            float ms = 0.f;
-            try {
-                apply_phi_adj_phi(p, x, o, 0, s);  // warm-up
-                RIMO_CUDA(cudaEventRecord(e0, s));
-                for (int r = 0; r < 3; ++r) apply_phi_adj_phi(p, x, o, 0, s);
-                RIMO_CUDA(cudaEventRecord(e1, s));
-                RIMO_CUDA(cudaEventSynchronize(e1));
-                RIMO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            } catch (...) {
-                rimo_plan_destroy(p);
-                throw;
-            }
-            rimo_plan_destroy(p);
-            const double t = ms / 3.0;
-            if (ms_out) ms_out[c] = t;
-            if (t < best) {
-                best = t;
-                pick = cands[c];
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    } catch (...) {
-        cudaFree(x);
-        cudaFree(o);
-        throw;
-    }
-    cudaFree(x);
-    cudaFree(o);
-    *tile_out = pick;
+    const std::vector<std::pair<int, int>> cands = {{32, base->uv_order}, {64, base->uv_order}};
+    double ms[2] = {-1.0, -1.0};
+    const int pick = tune(uvw, M, base, cands, stream, ms);
+    if (ms_out) ms_out[0] = ms[0], ms_out[1] = ms[1];
+    *tile_out = cands[pick].first;
     if (cache_path && *cache_path) {
-        cache[key] = pick;
+        cache[key] = *tile_out;
+        write_cache(cache_path, cache);
+    }
+    RIMO_API_END
+}
+
+rimo_status rimo_autotune(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
+                          void* stream, int32_t* tile_out, int32_t* order_out, double* ms_out) {
+    RIMO_API_BEGIN
+    if (!uvw || M <= 0 || !base || !tile_out || !order_out) fail(RIMO_ERR_INVALID_ARG, "null argument or empty data");
+    if (ms_out)
+        for (int i = 0; i < 6; ++i) ms_out[i] = -1.0;
+    const std::string key = shape_key(uvw, M, base, "_tile_order");
+    std::map<std::string, int> cache;
+    if (cache_path && *cache_path) {
+        cache = read_cache(cache_path);
+        auto it = cache.find(key);
+        if (it != cache.end() && (it->second / 10 == 32 || it->second / 10 == 64) && it->second % 10 <= 2) {
+            *tile_out = it->second / 10;
+            *order_out = it->second % 10;
+            return RIMO_OK;
+        }
+    }
+    std::vector<std::pair<int, int>> cands;
+    for (int t : {32, 64})
+        for (int o = 0; o < 3; ++o) cands.push_back({t, o});
+    double ms[6];
+    const int pick = tune(uvw, M, base, cands, stream, ms);
+    if (ms_out)
+        for (int i = 0; i < 6; ++i) ms_out[i] = ms[i];
+    *tile_out = cands[pick].first;
+    *order_out = cands[pick].second;
+    if (cache_path && *cache_path) {
+        cache[key] = *tile_out * 10 + *order_out;
         write_cache(cache_path, cache);
     }
     RIMO_API_END

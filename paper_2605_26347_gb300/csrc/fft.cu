@@ -388,24 +388,67 @@ struct RowSel {
     uint16_t row[256];
 };
 
-__device__ __forceinline__ int sel_row0(const RowSel& sel, int rows_per_blk) {
-    const int b = (int)blockIdx.x;
+__device__ __forceinline__ int sel_row0(const RowSel& sel, int b, int rows_per_blk) {
     return sel.on ? ((int)sel.row[b / sel.bpt] * sel.bpt + b % sel.bpt) * rows_per_blk : b * rows_per_blk;
 }
 
+// ----------------------------------------------------------------------------- jobs
+// A pass over one (plan, w-bin) is a job.  A launch covers one job (the applies of a plan,
+// bin after bin: the job's arguments by value) or a table of jobs of the same transform
+// shape (a wideband batch, every channel's every bin in one launch per pass): job j owns
+// the launch's blocks [first[j], first[j + 1]), and a block finds its job by bisection and
+// then runs as in a one-job launch, with its block index within the job.
+struct RowsJob {          // a rows pass: image rows -> transposed half transforms, or back
+    const float2* in;
+    float2* out;
+    ZArgs z;
+    RowSel sel;
+};
+struct ColsJob {          // a cols pass over the selected grid rows
+    const float2* in;
+    float2* out;
+    const uint8_t* need;  // [tu * ntv + tv] of the job's bin: the tile is read or stored
+    RowSel sel;
+};
+template <class J>
+struct JobTable {
+    const J* jobs;
+    const int* first;     // njobs + 1 block offsets (multiples of the cluster size)
+    int njobs;
+};
+
+// This block's job and its block index b within the job.
+template <bool TABLE, class J>
+__device__ __forceinline__ const J& block_job(const J& one, const JobTable<J>& tab, int& b) {
+    b = (int)blockIdx.x;
+    if constexpr (TABLE) {
+        const int j = job_of(tab.first, tab.njobs, b);
+        b -= __ldg(tab.first + j);
+        return tab.jobs[j];
+    } else {
+        (void)tab;
+        return one;
+    }
+}
+
 // ----------------------------------------------------------------------------- forward rows
-// grid: ny / RB blocks of RB * N/8 threads; block b transforms image rows [b RB, b RB + RB):
-// Z_p times the row, zero-padded to 2N, DFT along l; row i of the result is column i of
-// At (At[k][i], k < 2N).
-template <int N, int RB, int C>
+// grid: ny / RB blocks of RB * N/8 threads per job; block b transforms image rows
+// [b RB, b RB + RB): Z_p times the row, zero-padded to 2N, DFT along l; row i of the result
+// is column i of At (At[k][i], k < 2N).
+template <int N, int RB, int C, bool TABLE>
 __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
-    fwd_rows_kernel(const float2* __restrict__ x, float2* __restrict__ At, int ny, ZArgs z,
-                    const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
+    fwd_rows_kernel(const __grid_constant__ RowsJob one, const JobTable<RowsJob> tab, int ny,
+                    const float2* __restrict__ tws) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
+    int bk;
+    const RowsJob& J = block_job<TABLE>(one, tab, bk);
+    const float2* __restrict__ x = J.in;
+    const ZArgs z = J.z;
+    const RowSel& sel = J.sel;
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const int i = blockIdx.x * RB + g;
+    const int i = bk * RB + g;
     const int ic = i - ny / 2;
     const float2* xr = x + (size_t)i * N;
     float2 v[16];
@@ -427,27 +470,29 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
     transposed_store<RB, C, SR, L, RB * N / 8>(
         smem, [](int kk) { return kk; }, [](int kk) { return kk; },
         [&](int kk) { return !sel.on || ((sel.bits[(kk >> sel.shift) >> 5] >> ((kk >> sel.shift) & 31)) & 1u); },
-        At, (size_t)ny, (int)blockIdx.x * RB);
+        J.out, (size_t)ny, bk * RB);
 }
 
 // ----------------------------------------------------------------------------- forward cols
-// grid: gx / RG blocks; row u of At (N = ny samples) -> X[u][0 .. 2N)
-// need[tu * ntv + tv] != 0 marks the tiles of X some active patch reads; the rest of X is
-// never read and not stored.
-template <int N, int RG>
+// grid: the selected grid rows / RG blocks per job; row u of At (N = ny samples) ->
+// X[u][0 .. 2N).  Tiles of X that no active patch reads are not stored.
+template <int N, int RG, bool TABLE>
 __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
-    fwd_cols_kernel(const float2* __restrict__ At, float2* __restrict__ X, const uint8_t* __restrict__ need,
-                    int shift, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
+    fwd_cols_kernel(const __grid_constant__ ColsJob one, const JobTable<ColsJob> tab, int shift,
+                    const float2* __restrict__ tws) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
+    int bk;
+    const ColsJob& J = block_job<TABLE>(one, tab, bk);
+    const uint8_t* __restrict__ need = J.need;
     const int ntv = L >> shift;
     uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RG * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const int r0 = sel_row0(sel, RG);
+    const int r0 = sel_row0(J.sel, bk, RG);
     const size_t u = (size_t)r0 + g;
-    const float2* in = At + u * N;
-    float2* out = X + u * L;
+    const float2* __restrict__ in = J.in + u * N;
+    float2* __restrict__ out = J.out + u * L;
     for (int e = threadIdx.x; e < RG * ntv; e += blockDim.x) {
         const size_t uu = (size_t)r0 + e / ntv;
         s_need[e] = need[(uu >> shift) * ntv + e % ntv];
@@ -485,45 +530,53 @@ struct FoldArgs {
     int ntu, ntv, TS, H, PW, gy;
 };
 
-__global__ void __launch_bounds__(256) fold_kernel(FoldArgs F) {
-    const int tile = F.tiles[blockIdx.x];
+template <bool TABLE>
+__global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ FoldArgs one, const JobTable<FoldArgs> tab) {
+    int bk;
+    const FoldArgs& F = block_job<TABLE>(one, tab, bk);
+    const int tile = F.tiles[bk];
     const int tu = tile / F.ntv, tv = tile - tu * F.ntv;
     const int tu1 = tu == 0 ? F.ntu - 1 : tu - 1, tv1 = tv == 0 ? F.ntv - 1 : tv - 1;
     const size_t np = (size_t)F.PW * F.PW;
     const int s00 = F.slot[tu * F.ntv + tv], s10 = F.slot[tu1 * F.ntv + tv];
     const int s01 = F.slot[tu * F.ntv + tv1], s11 = F.slot[tu1 * F.ntv + tv1];
+    const float2* __restrict__ patch = F.patch;
+    float2* __restrict__ Xh = F.Xh;
     for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
         const int a = e / F.TS, b = e - a * F.TS;
         float2 acc = make_float2(0.f, 0.f);
-        if (s00 >= 0) acc = F.patch[s00 * np + a * F.PW + b];
-        if (a < F.H && s10 >= 0) acc = cadd(acc, F.patch[s10 * np + (a + F.TS) * F.PW + b]);
-        if (b < F.H && s01 >= 0) acc = cadd(acc, F.patch[s01 * np + a * F.PW + b + F.TS]);
-        if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, F.patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
-        F.Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
+        if (s00 >= 0) acc = patch[s00 * np + a * F.PW + b];
+        if (a < F.H && s10 >= 0) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
+        if (b < F.H && s01 >= 0) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
+        if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
+        Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
     }
 }
 
 // ----------------------------------------------------------------------------- inverse cols
-// grid: gx / RB blocks; rows u of Xh (2N cells along v; cells of tiles without a mark in
-// need[] are zero and not read) -> B[i][u] for the N image rows i.
-template <int N, int RB, int C>
+// grid: the selected grid rows / RB blocks per job; rows u of Xh (2N cells along v; cells
+// of tiles without a mark in need[] are zero and not read) -> B[i][u] for the N image rows i.
+template <int N, int RB, int C, bool TABLE>
 __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 / (RB * N / 8)) : 1)
-    inv_cols_kernel(const float2* __restrict__ Xh, float2* __restrict__ B, int gx, const uint8_t* __restrict__ need,
-                    int shift, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
+    inv_cols_kernel(const __grid_constant__ ColsJob one, const JobTable<ColsJob> tab, int gx, int shift,
+                    const float2* __restrict__ tws) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
+    int bk;
+    const ColsJob& J = block_job<TABLE>(one, tab, bk);
+    const uint8_t* __restrict__ need = J.need;
     const int ntv = L >> shift;
     uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + RB * SR);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const int r0 = sel_row0(sel, RB);
+    const int r0 = sel_row0(J.sel, bk, RB);
     const int u = r0 + g;
     for (int e = threadIdx.x; e < RB * ntv; e += blockDim.x) {
         const int uu = r0 + e / ntv;
         s_need[e] = need[(size_t)(uu >> shift) * ntv + e % ntv];
     }
     __syncthreads();
-    const float2* in = Xh + (size_t)u * L;
+    const float2* __restrict__ in = J.in + (size_t)u * L;
     float2 v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -536,47 +589,66 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
     // kept output kk < N: k = kk (kk < N/2) or kk + N; image row i = (k < N/2 ? k : k - L) + N/2
     transposed_store<RB, C, SR, N, RB * N / 8>(
         smem, [](int kk) { return kk < N / 2 ? kk : kk + N; },
-        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, [](int) { return true; }, B, (size_t)gx, r0);
+        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, [](int) { return true; }, J.out, (size_t)gx,
+        r0);
 }
 
 // ----------------------------------------------------------------------------- inverse rows
-// grid: ny / RG blocks; row i of B (2N cells along u) -> out[i][0 .. N) * conj(Z_p)
-template <int N, int RG>
+// grid: ny / RG blocks; row i of B (2N cells along u) -> out[i][0 .. N) * conj(Z_p).
+// With a table the grid is groups x ny / RG blocks: group c (the w-bins of one channel of a
+// batch, jobs [group[c], group[c + 1])) has its bins summed into its image by the same
+// block, one bin after the other (Sigma_p of Eq. 7 without a race or a second pass).
+template <int N, int RG, bool TABLE>
 __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 / (RG * N / 8)) : 1)
-    inv_rows_kernel(const float2* __restrict__ B, float2* __restrict__ out, int ny, ZArgs z, int accumulate,
-                    int real_only, const float2* __restrict__ tws, const __grid_constant__ RowSel sel) {
+    inv_rows_kernel(const __grid_constant__ RowsJob one, const JobTable<RowsJob> tab, const int* __restrict__ group,
+                    int ny, int accumulate, int real_only, const float2* __restrict__ tws) {
     constexpr int L = 2 * N, T = L / 16, SR = L + L / 16;
     extern __shared__ float2 smem[];
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* sm = smem + g * SR;
-    const int i = blockIdx.x * RG + g;
+    int bk = (int)blockIdx.x, j0 = 0, j1 = 1;
+    if constexpr (TABLE) {
+        const int per = ny / RG, c = bk / per;
+        bk -= c * per;
+        j0 = __ldg(group + c);
+        j1 = __ldg(group + c + 1);
+    }
+    const int i = bk * RG + g;
     const int ic = i - ny / 2;
-    const float2* in = B + (size_t)i * L;
-    float2* orow = out + (size_t)i * N;
-    float2 v[16];
-    // columns u of tile rows the inverse column pass skipped are zero (not stored)
-    uint32_t keep = 0xffffu;
-    if (sel.on) {
-        keep = 0;
+    for (int jj = j0; jj < j1; ++jj) {
+        const RowsJob& J = TABLE ? tab.jobs[jj] : one;
+        const RowSel& sel = J.sel;
+        const ZArgs z = J.z;
+        const float2* __restrict__ in = J.in + (size_t)i * L;
+        float2* __restrict__ orow = J.out + (size_t)i * N;
+        const int acc = accumulate || jj > j0;
+        float2 v[16];
+        // columns u of tile rows the inverse column pass skipped are zero (not stored)
+        uint32_t keep = 0xffffu;
+        if (sel.on) {
+            keep = 0;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int tr = (t + T * m) >> sel.shift;
+                keep |= ((sel.bits[tr >> 5] >> (tr & 31)) & 1u) << m;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = (keep >> m) & 1u ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
+        fft_n<L, true>(v, sm, t, tws);
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
-            const int tr = (t + T * m) >> sel.shift;
-            keep |= ((sel.bits[tr >> 5] >> (tr & 31)) & 1u) << m;
+            const int k = t + T * m;
+            if (k >= N / 2 && k < 3 * N / 2) continue;  // outside the crop
+            const int jc = k < N / 2 ? k : k - L;
+            const int j = jc + N / 2;
+            float2 val = cmulc(v[out_slot<L>(m)], z_factor(z, i, j, ic, jc));
+            if (acc) val = cadd(val, orow[j]);
+            if (real_only) val.y = 0.f;
+            orow[j] = val;
         }
-    }
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = (keep >> m) & 1u ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
-    fft_n<L, true>(v, sm, t, tws);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const int k = t + T * m;
-        if (k >= N / 2 && k < 3 * N / 2) continue;  // outside the crop
-        const int jc = k < N / 2 ? k : k - L;
-        const int j = jc + N / 2;
-        float2 val = cmulc(v[out_slot<L>(m)], z_factor(z, i, j, ic, jc));
-        if (accumulate) val = cadd(val, orow[j]);
-        if (real_only) val.y = 0.f;
-        orow[j] = val;
+        // the next bin's first stage rewrites the exchange buffer this one's last stage read
+        if (jj + 1 < j1) __syncthreads();
     }
 }
 
@@ -693,87 +765,273 @@ static RowSel inv_sel(const rimo_plan* p, int bin) {
     return row_sel(p, bin, C * RB <= p->TS ? RB : p->TS + 1);
 }
 
-template <int N>
-static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
+static RowsJob rows_job(const rimo_plan* p, int bin, const float2* in, float2* out, const RowSel& sel) {
+    RowsJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.in = in;
+    J.out = out;
+    J.z = zargs(p, bin);
+    J.sel = sel;
+    return J;
+}
+static ColsJob cols_job(const rimo_plan* p, int bin, const float2* in, float2* out, const RowSel& sel) {
+    ColsJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.in = in;
+    J.out = out;
+    J.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * (p->gy / p->TS);
+    J.sel = sel;
+    return J;
+}
+// grid-step patches (one per active tile, merged) or holographic-apply patches (one per
+// needed tile): both cover [tile origin, + PW) on each axis
+static FoldArgs fold_args(const rimo_plan* p, int bin, const float2* patch, const int* slot, float2* Xh) {
+    const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
+    FoldArgs F;
+    F.patch = patch;
+    F.slot = slot + (size_t)bin * ntu * ntv;
+    F.tiles = p->d_need_list + p->bins[bin].n0;
+    F.Xh = Xh;
+    F.ntu = ntu;
+    F.ntv = ntv;
+    F.TS = p->TS;
+    F.H = p->H;
+    F.PW = p->PW;
+    F.gy = p->gy;
+    return F;
+}
+static int tile_shift(int TS) { return TS == 64 ? 6 : 5; }
+
+// One launch of each pass, for one job (TABLE = false: `one`) or a job table.
+template <int N, bool TABLE>
+static void run_fwd_rows(const RowsJob& one, const JobTable<RowsJob>& tab, int grid, int ny, const float2* tws,
+                         cudaStream_t s) {
     constexpr int RB = rows_per_block<N>();
     constexpr int C = cluster_of<RB>();
     const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2);
-    const int grid = p->ny / RB;
+    if (grid == 0) return;
     if constexpr (C > 1) {
         if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "image rows do not fill the transposed-store clusters");
-        set_smem(fwd_rows_kernel<N, RB, C>, sm);
-        launch_clustered(fwd_rows_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, x, At, p->ny, zargs(p, bin),
-                         (const float2*)p->tab.tws_x, fwd_sel(p, bin));
+        set_smem(fwd_rows_kernel<N, RB, C, TABLE>, sm);
+        launch_clustered(fwd_rows_kernel<N, RB, C, TABLE>, grid, RB * N / 8, sm, C, s, one, tab, ny, tws);
     } else {
-        set_smem(fwd_rows_kernel<N, RB, 1>, sm);
-        fwd_rows_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(x, At, p->ny, zargs(p, bin), p->tab.tws_x,
-                                                               fwd_sel(p, bin));
+        set_smem(fwd_rows_kernel<N, RB, 1, TABLE>, sm);
+        fwd_rows_kernel<N, RB, 1, TABLE><<<grid, RB * N / 8, sm, s>>>(one, tab, ny, tws);
     }
+}
+
+template <int N, bool TABLE>
+static void run_fwd_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int grid, int TS, const float2* tws,
+                         cudaStream_t s) {
+    constexpr int RG = rows_per_block<N>();
+    const int ntv = (2 * N) / TS;
+    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
+    if (grid == 0) return;
+    set_smem(fwd_cols_kernel<N, RG, TABLE>, sm);
+    fwd_cols_kernel<N, RG, TABLE><<<grid, RG * N / 8, sm, s>>>(one, tab, tile_shift(TS), tws);
+}
+
+template <bool TABLE>
+static void run_fold(const FoldArgs& one, const JobTable<FoldArgs>& tab, int grid, cudaStream_t s) {
+    if (grid == 0) return;
+    fold_kernel<TABLE><<<grid, 256, 0, s>>>(one, tab);
+}
+
+template <int N, bool TABLE>
+static void run_inv_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int grid, int gx, int TS,
+                         const float2* tws, cudaStream_t s) {
+    constexpr int RB = rows_per_block<N>();
+    constexpr int C = cluster_of<RB>();
+    const int ntv = (2 * N) / TS;
+    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2) + (size_t)RB * ntv + 16;
+    if (grid == 0) return;
+    // C consecutive blocks of a cluster stay in one tile row: TS / RB is a multiple of C
+    if constexpr (C > 1) {
+        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
+        set_smem(inv_cols_kernel<N, RB, C, TABLE>, sm);
+        launch_clustered(inv_cols_kernel<N, RB, C, TABLE>, grid, RB * N / 8, sm, C, s, one, tab, gx, tile_shift(TS),
+                         tws);
+    } else {
+        set_smem(inv_cols_kernel<N, RB, 1, TABLE>, sm);
+        inv_cols_kernel<N, RB, 1, TABLE><<<grid, RB * N / 8, sm, s>>>(one, tab, gx, tile_shift(TS), tws);
+    }
+}
+
+template <int N, bool TABLE>
+static void run_inv_rows(const RowsJob& one, const JobTable<RowsJob>& tab, const int* group, int grid, int ny, int acc,
+                         int re, const float2* tws, cudaStream_t s) {
+    constexpr int RG = rows_per_block<N>();
+    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2);
+    if (grid == 0) return;
+    set_smem(inv_rows_kernel<N, RG, TABLE>, sm);
+    inv_rows_kernel<N, RG, TABLE><<<grid, RG * N / 8, sm, s>>>(one, tab, group, ny, acc, re, tws);
+}
+
+template <class J>
+static JobTable<J> no_table() {
+    JobTable<J> t;
+    t.jobs = nullptr;
+    t.first = nullptr;
+    t.njobs = 0;
+    return t;
+}
+
+template <int N>
+static void fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {
+    run_fwd_rows<N, false>(rows_job(p, bin, x, At, fwd_sel(p, bin)), no_table<RowsJob>(),
+                           p->ny / rows_per_block<N>(), p->ny, p->tab.tws_x, s);
 }
 
 template <int N>
 static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
-    constexpr int RG = rows_per_block<N>();
-    const int ntv = (2 * N) / p->TS;
-    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
-    set_smem(fwd_cols_kernel<N, RG>, sm);
-    const size_t ntile = (size_t)(p->gx / p->TS) * (p->gy / p->TS);
     const RowSel sel = fwd_sel(p, bin);
-    const int grid = sel_blocks(p, bin, sel, RG);
-    if (grid == 0) return;
-    fwd_cols_kernel<N, RG><<<grid, RG * N / 8, sm, s>>>(At, X, p->d_need + (size_t)bin * ntile,
-                                                        p->TS == 64 ? 6 : 5, p->tab.tws_y, sel);
+    run_fwd_cols<N, false>(cols_job(p, bin, At, X, sel), no_table<ColsJob>(),
+                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->TS, p->tab.tws_y, s);
 }
 
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStream_t s) {
-    constexpr int RB = rows_per_block<N>();
-    constexpr int C = cluster_of<RB>();
-    const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
-    const size_t ntile = (size_t)ntu * ntv;
-    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2) + (size_t)RB * ntv + 16;
     const auto& br = p->bins[bin];
-    if (br.n1 > br.n0) {
-        FoldArgs F;
-        // grid-step patches (one per active tile, merged) or holographic-apply patches
-        // (one per needed tile): both cover [tile origin, + PW) on each axis
-        F.patch = holo ? p->d_hpatch : p->d_patch;
-        F.slot = (holo ? p->d_hslot : p->d_slot) + (size_t)bin * ntile;
-        F.tiles = p->d_need_list + br.n0;
-        F.Xh = p->d_X;
-        F.ntu = ntu;
-        F.ntv = ntv;
-        F.TS = p->TS;
-        F.H = p->H;
-        F.PW = p->PW;
-        F.gy = p->gy;
-        fold_kernel<<<br.n1 - br.n0, 256, 0, s>>>(F);
-    }
-    const int shift = p->TS == 64 ? 6 : 5;
-    const uint8_t* need = p->d_need + (size_t)bin * ntile;
-    // C consecutive blocks of a cluster stay in one tile row: TS / RB is a multiple of C
+    run_fold<false>(fold_args(p, bin, holo ? p->d_hpatch : p->d_patch, holo ? p->d_hslot : p->d_slot, p->d_X),
+                    no_table<FoldArgs>(), br.n1 - br.n0, s);
     const RowSel sel = inv_sel(p, bin);
-    const int grid = sel_blocks(p, bin, sel, RB);
-    if (grid == 0) return;
-    if constexpr (C > 1) {
-        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
-        set_smem(inv_cols_kernel<N, RB, C>, sm);
-        launch_clustered(inv_cols_kernel<N, RB, C>, grid, RB * N / 8, sm, C, s, (const float2*)p->d_X, B, p->gx,
-                         need, shift, (const float2*)p->tab.tws_y, sel);
-    } else {
-        set_smem(inv_cols_kernel<N, RB, 1>, sm);
-        inv_cols_kernel<N, RB, 1><<<grid, RB * N / 8, sm, s>>>(p->d_X, B, p->gx, need, shift, p->tab.tws_y, sel);
-    }
+    run_inv_cols<N, false>(cols_job(p, bin, p->d_X, B, sel), no_table<ColsJob>(),
+                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->gx, p->TS, p->tab.tws_y, s);
 }
 
 template <int N>
 static void inv_rows(const rimo_plan* p, int bin, const float2* B, float2* out, int acc, int re,
                      cudaStream_t s) {
-    constexpr int RG = rows_per_block<N>();
-    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2);
-    set_smem(inv_rows_kernel<N, RG>, sm);
-    inv_rows_kernel<N, RG><<<p->ny / RG, RG * N / 8, sm, s>>>(B, out, p->ny, zargs(p, bin), acc, re, p->tab.tws_x,
-                                                            inv_sel(p, bin));
+    run_inv_rows<N, false>(rows_job(p, bin, B, out, inv_sel(p, bin)), no_table<RowsJob>(), nullptr,
+                           p->ny / rows_per_block<N>(), p->ny, acc, re, p->tab.tws_x, s);
+}
+
+// ----------------------------------------------------------------------------- job tables
+// The transform passes of a stage-batched apply: one launch per pass over every job.
+struct WideFft {
+    int nx = 0, ny = 0, gx = 0, TS = 0, ngroups = 0;
+    const float2* tws_x = nullptr;
+    const float2* tws_y = nullptr;
+    struct Pass {
+        void* jobs = nullptr;
+        int* first = nullptr;
+        int njobs = 0, blocks = 0;
+    };
+    Pass rows_fwd, cols_fwd, fold, cols_inv, rows_inv;
+    int* group = nullptr;  // rows_inv: jobs of channel c are [group[c], group[c + 1])
+    std::vector<void*> owned;
+    ~WideFft() {
+        for (void* q : owned) cudaFree(q);
+    }
+};
+
+template <class J>
+static WideFft::Pass upload_pass(WideFft* w, const std::vector<J>& jobs, const std::vector<int>& first,
+                                 cudaStream_t s) {
+    WideFft::Pass ps;
+    ps.njobs = (int)jobs.size();
+    ps.blocks = first.empty() ? 0 : first.back();
+    if (jobs.empty()) return ps;
+    void* dj = nullptr;
+    void* df = nullptr;
+    RIMO_CUDA(cudaMalloc(&dj, jobs.size() * sizeof(J)));
+    w->owned.push_back(dj);
+    RIMO_CUDA(cudaMalloc(&df, first.size() * sizeof(int)));
+    w->owned.push_back(df);
+    RIMO_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(J), cudaMemcpyHostToDevice, s));
+    RIMO_CUDA(cudaMemcpyAsync(df, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    ps.jobs = dj;
+    ps.first = (int*)df;
+    return ps;
+}
+
+WideFft* wide_fft_create(const std::vector<WideJob>& jobs, const std::vector<const float2*>& x,
+                         const std::vector<float2*>& out, cudaStream_t s) {
+    if (jobs.empty()) fail(RIMO_ERR_INVALID_ARG, "no jobs");
+    auto* w = new WideFft();
+    try {
+        const rimo_plan* p0 = jobs[0].p;
+        w->nx = p0->nx;
+        w->ny = p0->ny;
+        w->gx = p0->gx;
+        w->TS = p0->TS;
+        w->tws_x = p0->tab.tws_x;
+        w->tws_y = p0->tab.tws_y;
+        w->ngroups = (int)x.size();
+        const int rb = 4096 / p0->nx;  // rows per block of every pass (nx = ny)
+        std::vector<RowsJob> rf, ri;
+        std::vector<ColsJob> cf, ci;
+        std::vector<FoldArgs> fo;
+        std::vector<int> frf{0}, fcf{0}, ffo{0}, fci{0}, grp(w->ngroups + 1, 0);
+        for (const WideJob& j : jobs) {
+            const rimo_plan* p = j.p;
+            const RowSel fs = fwd_sel(p, j.bin), is = inv_sel(p, j.bin);
+            rf.push_back(rows_job(p, j.bin, x[j.group], j.AB, fs));
+            frf.push_back(frf.back() + p->ny / rb);
+            cf.push_back(cols_job(p, j.bin, j.AB, j.X, fs));
+            fcf.push_back(fcf.back() + sel_blocks(p, j.bin, fs, rb));
+            fo.push_back(fold_args(p, j.bin, j.patch, p->d_slot, j.X));
+            ffo.push_back(ffo.back() + (p->bins[j.bin].n1 - p->bins[j.bin].n0));
+            ci.push_back(cols_job(p, j.bin, j.X, j.AB, is));
+            fci.push_back(fci.back() + sel_blocks(p, j.bin, is, rb));
+            ri.push_back(rows_job(p, j.bin, j.AB, out[j.group], is));
+            grp[j.group + 1]++;
+        }
+        for (int c = 0; c < w->ngroups; ++c) grp[c + 1] += grp[c];
+        w->rows_fwd = upload_pass(w, rf, frf, s);
+        w->cols_fwd = upload_pass(w, cf, fcf, s);
+        w->fold = upload_pass(w, fo, ffo, s);
+        w->cols_inv = upload_pass(w, ci, fci, s);
+        w->rows_inv = upload_pass(w, ri, std::vector<int>{0, w->ngroups * (p0->ny / rb)}, s);
+        RIMO_CUDA(cudaMalloc(&w->group, grp.size() * sizeof(int)));
+        w->owned.push_back(w->group);
+        RIMO_CUDA(cudaMemcpyAsync(w->group, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    } catch (...) {
+        delete w;
+        throw;
+    }
+    return w;
+}
+
+void wide_fft_destroy(WideFft* w) { delete w; }
+
+template <class J>
+static JobTable<J> table_of(const WideFft::Pass& ps) {
+    JobTable<J> t;
+    t.jobs = (const J*)ps.jobs;
+    t.first = ps.first;
+    t.njobs = ps.njobs;
+    return t;
+}
+
+template <int N>
+static void wide_fwd_n(const WideFft* w, cudaStream_t s) {
+    RowsJob r1;
+    ColsJob c1;
+    std::memset(&r1, 0, sizeof(r1));
+    std::memset(&c1, 0, sizeof(c1));
+    run_fwd_rows<N, true>(r1, table_of<RowsJob>(w->rows_fwd), w->rows_fwd.blocks, w->ny, w->tws_x, s);
+    run_fwd_cols<N, true>(c1, table_of<ColsJob>(w->cols_fwd), w->cols_fwd.blocks, w->TS, w->tws_y, s);
+}
+
+template <int N>
+static void wide_inv_n(const WideFft* w, int real_only, cudaStream_t s) {
+    RowsJob r1;
+    ColsJob c1;
+    FoldArgs f1;
+    std::memset(&r1, 0, sizeof(r1));
+    std::memset(&c1, 0, sizeof(c1));
+    std::memset(&f1, 0, sizeof(f1));
+    run_fold<true>(f1, table_of<FoldArgs>(w->fold), w->fold.blocks, s);
+    run_inv_cols<N, true>(c1, table_of<ColsJob>(w->cols_inv), w->cols_inv.blocks, w->gx, w->TS, w->tws_y, s);
+    run_inv_rows<N, true>(r1, table_of<RowsJob>(w->rows_inv), w->group, w->rows_inv.blocks, w->ny, 0, real_only,
+                          w->tws_x, s);
+}
+
+void wide_fwd(const WideFft* w, cudaStream_t s) { RIMO_DISPATCH_N(w->nx, wide_fwd_n<NN>(w, s)); }
+void wide_inv(const WideFft* w, int real_only, cudaStream_t s) {
+    RIMO_DISPATCH_N(w->nx, wide_inv_n<NN>(w, real_only, s));
 }
 
 void launch_fwd_rows(const rimo_plan* p, int bin, const float2* x, float2* At, cudaStream_t s) {

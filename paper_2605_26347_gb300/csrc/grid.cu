@@ -89,23 +89,31 @@ constexpr int GTG_NBUF = 4;   // maximum depth of the tap ring (the plan may use
 constexpr int GTG_HDR = 256;  // shared-memory header: the ring's and the X buffers' mbarriers
 constexpr int GTG_CV = GTG_CHUNK;  // visibilities per chunk (one per consumer warp)
 
-struct GtgArgs {
-    const TileDesc* units;  // this bin's work units, in patch-slot order
-    const int* sched;       // unit indices, heaviest first
+// The per-bin side of a grid-step launch: one (plan, w-bin) job.
+struct GtgJob {
+    const TileDesc* units;  // the bin's work units, in patch-slot order
     const ChunkDesc* chunks;
-    int nunits;
     const VisMeta* meta;
     const float2* const* gblk;
     const float2* X;        // forward grid [gx][gy]
     float2* patch;          // accumulator patch per unit slot
+    const uint32_t* fx;     // fixed-point bounds (tap bounds; maxterm of a Phi^dagger apply)
+    const uint8_t* need;    // [tile] of this bin: some footprint reaches the tile
+    int* status;            // the plan's device status word
+    int PW;                 // the plan's patch side (TS + largest tile side - 1)
+};
+
+struct GtgArgs {
+    GtgJob one;             // a one-bin launch: the bin
+    const int* sched;       //   its unit slots, heaviest first
+    const GtgJob* jobs;     // a stage-batched launch: every (plan, bin) of the batch
+    const int2* queue;      //   (job, unit slot) of every unit of every job, heaviest first
+    int nunits;             // units of the launch (schedule or queue length)
     const float2* y_in;
     float2* y_out;
     int gx, gy, TS, PW;
     int chunk_bytes;
     int nbuf;               // ring depth in use, 2..GTG_NBUF
-    int* status;
-    const uint32_t* fx;     // fixed-point bounds (tap bounds; maxterm of a Phi^dagger apply)
-    const uint8_t* need;    // [tile] of this bin: some footprint reaches the tile
     int ntv, shift;
     int prefetch;           // the producer bulk-copies the next unit's X patch (double buffer)
     // failure-detection test (rimo_plan_set_wait_test): the consumers withhold their release
@@ -113,6 +121,19 @@ struct GtgArgs {
     int stall;
     uint32_t peer_polls;    // poll limit of the producer's waits on other warps (empty, xfree)
 };
+
+// The job and the patch slot of the launch's unit idx.
+template <bool TABLE>
+__device__ __forceinline__ const GtgJob* unit_job(const GtgArgs& A, int idx, int& slot) {
+    if constexpr (TABLE) {
+        const int2 q = A.queue[idx];
+        slot = q.y;
+        return A.jobs + q.x;
+    } else {
+        slot = A.sched[idx];
+        return &A.one;
+    }
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -260,8 +281,9 @@ __device__ __forceinline__ void vis_dispatch(int S, const float2* T, const float
 // Only unit boundaries (patch load / store) synchronise all consumers.
 // MODE 0: de-grid (y_out), 1: grid (y_in), 2: fused de-grid + grid; PWC: the patch side
 // when known at compile time (the common plans), else 0
-template <int MODE, int PWC>
-__global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
+// TABLE: the units of many (plan, bin) jobs from one queue (a stage-batched wideband apply).
+template <int MODE, int PWC, bool TABLE>
+__global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_constant__ GtgArgs A) {
     constexpr bool GATHER = MODE != 1, SCATTER = MODE != 0;
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
@@ -270,14 +292,16 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     uint64_t* xfree = xfull + 2;         // [2] consumers are done with the buffer
     VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + GTG_HDR);      // GTG_NBUF x GTG_CV entries
     float2* taps = reinterpret_cast<float2*>(smraw + GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta));
-    const int PW = PWC > 0 ? PWC : A.PW, npatch = PW * PW;
+    // shared memory laid out for the launch's largest patch (a staged batch's jobs may have
+    // different patch sides; every unit uses its own job's)
+    const int PWmax = PWC > 0 ? PWC : A.PW, npmax = PWmax * PWmax;
     const int chunk_f2 = A.chunk_bytes / 8;
     const uint32_t NB = (uint32_t)A.nbuf;
     const bool pre = GATHER && A.prefetch;
     float2* Xbuf0 = taps + (size_t)NB * chunk_f2;
-    float2* Xbuf1 = Xbuf0 + (pre ? npatch : 0);
-    int* Ahi = reinterpret_cast<int*>(Xbuf1 + (GATHER ? npatch : 0));  // [cell][re, im] words
-    int* Alo = Ahi + (SCATTER ? 2 * npatch : 0);
+    float2* Xbuf1 = Xbuf0 + (pre ? npmax : 0);
+    int* Ahi = reinterpret_cast<int*>(Xbuf1 + (GATHER ? npmax : 0));  // [cell][re, im] words
+    int* Alo = Ahi + (SCATTER ? 2 * npmax : 0);
     __shared__ volatile int s_abort;
     __shared__ float s_xmax[GTG_CONSUMERS];
 
@@ -304,15 +328,18 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         for (int r = 0;; ++r) {
             const int idx = unit_of(r, cb, G);
             if (idx >= A.nunits) break;
-            const TileDesc td = A.units[A.sched[idx]];
+            int slot;
+            const GtgJob* J = unit_job<TABLE>(A, idx, slot);
+            const TileDesc td = J->units[slot];
             const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
+            const int PW = PWC > 0 ? PWC : (TABLE ? J->PW : A.PW), npatch = PW * PW;
             if (pre) {
                 // X patch of this unit into buffer r & 1, once the consumers released it
                 // (unit r - 2); rows wrap along u, a row past the last column splits in two
                 const int j = r & 1;
                 if (r >= 2 && !s_abort && !mbar_wait_bounded(&xfree[j], ((r >> 1) - 1) & 1, A.peer_polls)) {
                     s_abort = 1;
-                    atomicExch(A.status, 1);
+                    atomicExch(J->status, 1);
                 }
                 if (s_abort) {
                     for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
@@ -327,19 +354,19 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                 for (int a = 0; a < PW; ++a) {
                     int gu = u0 + a;
                     if (gu >= A.gx) gu -= A.gx;
-                    const float2* row = A.X + (size_t)gu * A.gy;
+                    const float2* row = J->X + (size_t)gu * A.gy;
                     bulk_g2s(dst + a * PW, row + v0, (uint32_t)(n1 * sizeof(float2)), &xfull[j]);
                     if (n1 < PW) bulk_g2s(dst + a * PW + n1, row, (uint32_t)((PW - n1) * sizeof(float2)), &xfull[j]);
                 }
             }
             for (int c = 0; c < nchunks; ++c, ++g) {
-                const ChunkDesc cd = A.chunks[td.cb + c];
+                const ChunkDesc cd = J->chunks[td.cb + c];
                 const int64_t v0 = td.vb + (int64_t)c * GTG_CV;
                 const uint32_t nv = (uint32_t)((td.ve - v0) < GTG_CV ? (td.ve - v0) : GTG_CV);
                 const uint32_t b = g % NB, use = g / NB;
                 if (use > 0 && !s_abort && !mbar_wait_bounded(&empty[b], (use - 1) & 1, A.peer_polls)) {
                     s_abort = 1;
-                    atomicExch(A.status, 1);
+                    atomicExch(J->status, 1);
                 }
                 if (s_abort) {
                     // let the copies already in flight land before the block may exit
@@ -349,8 +376,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                     return;
                 }
                 mbar_arrive_expect_tx(&full[b], cd.bytes + nv * (uint32_t)sizeof(VisMeta));
-                bulk_g2s(mring + b * GTG_CV, A.meta + v0, nv * (uint32_t)sizeof(VisMeta), &full[b]);
-                bulk_g2s(taps + (size_t)b * chunk_f2, A.gblk[cd.block] + cd.off, cd.bytes, &full[b]);
+                bulk_g2s(mring + b * GTG_CV, J->meta + v0, nv * (uint32_t)sizeof(VisMeta), &full[b]);
+                bulk_g2s(taps + (size_t)b * chunk_f2, J->gblk[cd.block] + cd.off, cd.bytes, &full[b]);
             }
         }
         return;
@@ -361,15 +388,17 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
     for (int r = 0;; ++r) {
         const int idx = unit_of(r, cb, G);
         if (idx >= A.nunits) break;
-        const int slot = A.sched[idx];
-        const TileDesc td = A.units[slot];
+        int slot;
+        const GtgJob* J = unit_job<TABLE>(A, idx, slot);
+        const TileDesc td = J->units[slot];
         const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
+        const int PW = PWC > 0 ? PWC : (TABLE ? J->PW : A.PW), npatch = PW * PW;
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
         float xm = 0.f;
         float2* Xs = (r & 1) && pre ? Xbuf1 : Xbuf0;
         if (pre && !s_abort && !mbar_wait_or_abort(&xfull[r & 1], (r >> 1) & 1, &s_abort)) {
             s_abort = 1;
-            atomicExch(A.status, 1);
+            atomicExch(J->status, 1);
         }
         for (int a = warp; a < PW; a += GTG_CONSUMERS) {
             int gu = u0 + a;
@@ -384,7 +413,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
                         int gv = v0 + b;
                         if (gv >= A.gy) gv -= A.gy;
                         // cells of tiles no footprint reaches hold no grid values of this bin
-                        x = A.need[(gu >> A.shift) * A.ntv + (gv >> A.shift)] ? A.X[(size_t)gu * A.gy + gv]
+                        x = J->need[(gu >> A.shift) * A.ntv + (gv >> A.shift)] ? J->X[(size_t)gu * A.gy + gv]
                                                                               : make_float2(0.f, 0.f);
                         Xs[a * PW + b] = x;
                     }
@@ -410,19 +439,19 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
             float xmax = 0.f;
 #pragma unroll
             for (int w = 0; w < GTG_CONSUMERS; ++w) xmax = fmaxf(xmax, s_xmax[w]);
-            const float mt = 4.f * __uint_as_float(__ldg(A.fx + FX_TMAX)) * __uint_as_float(__ldg(A.fx + FX_T1)) * xmax;
+            const float mt = 4.f * __uint_as_float(__ldg(J->fx + FX_TMAX)) * __uint_as_float(__ldg(J->fx + FX_T1)) * xmax;
             fx_scale(mt, td.ve - td.vb, s1, inv_s1);
         } else if (SCATTER) {
             // twice tmax max|y|_1 (rounding margin); both words final before this launch
-            const float mt = 2.f * __uint_as_float(__ldcg(A.fx + FX_TMAX)) * __uint_as_float(__ldcg(A.fx + FX_YB));
-            if (!(mt <= 3.4028234e38f)) atomicExch(A.status, 3);
+            const float mt = 2.f * __uint_as_float(__ldcg(J->fx + FX_TMAX)) * __uint_as_float(__ldcg(J->fx + FX_YB));
+            if (!(mt <= 3.4028234e38f)) atomicExch(J->status, 3);
             fx_scale(mt, td.ve - td.vb, s1, inv_s1);
         }
         for (int c = 0; c < nchunks; ++c, ++g) {
             const uint32_t b = g % NB, par = (g / NB) & 1;
             if (!s_abort && !mbar_wait_or_abort(&full[b], par, &s_abort)) {
                 s_abort = 1;
-                atomicExch(A.status, 1);
+                atomicExch(J->status, 1);
             }
             const int64_t cv0 = td.vb + (int64_t)c * GTG_CV;
             const int ncv = (int)((td.ve - cv0) < GTG_CV ? (td.ve - cv0) : GTG_CV);
@@ -442,7 +471,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
         }
         consumers_sync();
         if (SCATTER && !s_abort) {
-            float2* dst = A.patch + (size_t)slot * npatch;
+            float2* dst = J->patch + (size_t)slot * npatch;
             const float inv_lo = inv_s1 * (1.f / 65536.f);
             for (int e = tid; e < npatch; e += GTG_CONSUMERS * 32) {
                 const int2 h = reinterpret_cast<const int2*>(Ahi)[e], l = reinterpret_cast<const int2*>(Alo)[e];
@@ -455,9 +484,27 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(GtgArgs A) {
 }
 
 // Adds the patches of the extra units of each split tile into its first unit's slot.
-__global__ void __launch_bounds__(256) merge_patches_kernel(float2* __restrict__ patch,
-                                                            const int2* __restrict__ groups, int npatch) {
-    const int2 gr = groups[blockIdx.x];
+// TABLE: job j (one (plan, bin) of a batch) owns blocks [first[j], first[j + 1]).
+struct MergeJob {
+    float2* patch;
+    const int2* groups;   // (first slot, units) of the bin's split tiles
+    int npatch;           // cells of one patch
+};
+
+template <bool TABLE>
+__global__ void __launch_bounds__(256) merge_patches_kernel(const __grid_constant__ MergeJob one,
+                                                            const MergeJob* __restrict__ jobs,
+                                                            const int* __restrict__ first, int njobs) {
+    int bk = (int)blockIdx.x;
+    const MergeJob* J = &one;
+    if constexpr (TABLE) {
+        const int j = job_of(first, njobs, bk);
+        bk -= __ldg(first + j);
+        J = jobs + j;
+    }
+    const int2 gr = J->groups[bk];
+    float2* patch = J->patch;
+    const int npatch = J->npatch;
     float2* dst = patch + (size_t)gr.x * npatch;
     for (int e = threadIdx.x; e < npatch; e += blockDim.x) {
         float2 acc = dst[e];
@@ -470,12 +517,59 @@ __global__ void __launch_bounds__(256) merge_patches_kernel(float2* __restrict__
     }
 }
 
-size_t gtg_smem(const rimo_plan* p, int mode, int nbuf, bool prefetch) {
-    const size_t npatch = (size_t)p->PW * p->PW * sizeof(float2);
+static size_t gtg_smem_dims(int PW, int chunk_bytes, int mode, int nbuf, bool prefetch) {
+    const size_t npatch = (size_t)PW * PW * sizeof(float2);
     // X patch (float2; two when prefetched) when de-gridding, hi + lo words (2 x int2) when gridding
     const int nx = mode != 1 ? (prefetch ? 2 : 1) : 0;
-    return GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * p->chunk_bytes +
+    return GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * chunk_bytes +
            (size_t)(nx + (mode != 0 ? 2 : 0)) * npatch;
+}
+
+size_t gtg_smem(const rimo_plan* p, int mode, int nbuf, bool prefetch) {
+    return gtg_smem_dims(p->PW, p->chunk_bytes, mode, nbuf, prefetch);
+}
+
+// Launch shape of the grid step for a patch side and tap-ring chunk (prefetch, ring
+// depth, shared memory); `mode` as in launch_gtg.
+static void gtg_shape(const rimo_plan* p, int PW, int chunk_bytes, int mode, GtgArgs& A, size_t& sm) {
+    const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
+    // prefetch the X patches when a double buffer still leaves a GTG_NBUF-deep tap ring
+    A.prefetch = mode != 1 && gtg_smem_dims(PW, chunk_bytes, mode, 4, true) <= limit;
+    A.nbuf = GTG_NBUF;
+    while (A.nbuf > 2 && gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch) > limit) --A.nbuf;
+    sm = gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch);
+    if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
+    A.gx = p->gx;
+    A.gy = p->gy;
+    A.TS = p->TS;
+    A.PW = PW;
+    A.chunk_bytes = chunk_bytes;
+    A.ntv = p->gy / p->TS;
+    A.shift = p->TS == 64 ? 6 : 5;
+    A.stall = p->test_stall;
+    A.peer_polls = p->test_stall ? p->test_polls : WAIT_POLLS;
+}
+
+static GtgJob gtg_job(const rimo_plan* p, int bin, const float2* X, float2* patch) {
+    GtgJob J;
+    J.units = p->d_tiles + p->bins[bin].t0;
+    J.chunks = p->d_chunks;
+    J.meta = p->d_meta;
+    J.gblk = p->d_gblock_ptrs;
+    J.X = X;
+    J.patch = patch;
+    J.fx = p->d_fx;
+    J.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * (p->gy / p->TS);
+    J.status = p->d_status;
+    J.PW = p->PW;
+    return J;
+}
+
+// the kernel instance: patch sides of the uv-tiles 32 and 64 with 15 x 15 tiles are
+// compile-time constants
+template <int MODE, bool TABLE>
+static void (*gtg_kernel_for(int PW))(GtgArgs) {
+    return PW == 46 ? gtg_kernel<MODE, 46, TABLE> : PW == 78 ? gtg_kernel<MODE, 78, TABLE> : gtg_kernel<MODE, 0, TABLE>;
 }
 
 template <int MODE>
@@ -484,43 +578,133 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     const int nu = br.t1 - br.t0;
     if (nu <= 0) return;
     GtgArgs A;
-    A.units = p->d_tiles + br.t0;
+    std::memset(&A, 0, sizeof(A));
+    A.one = gtg_job(p, bin, p->d_X, p->d_patch);
     A.sched = p->d_sched + br.t0;
-    A.chunks = p->d_chunks;
     A.nunits = nu;
-    A.meta = p->d_meta;
-    A.gblk = p->d_gblock_ptrs;
-    A.X = p->d_X;
-    A.patch = p->d_patch;
     A.y_in = y_in;
     A.y_out = y_out;
-    A.gx = p->gx;
-    A.gy = p->gy;
-    A.TS = p->TS;
-    A.PW = p->PW;
-    A.chunk_bytes = p->chunk_bytes;
-    A.status = p->d_status;
-    A.fx = p->d_fx;
-    A.ntv = p->gy / p->TS;
-    A.shift = p->TS == 64 ? 6 : 5;
-    A.need = p->d_need + (size_t)bin * (size_t)(p->gx / p->TS) * A.ntv;
-    const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
-    // prefetch the X patches when a double buffer still leaves a GTG_NBUF-deep tap ring
-    A.prefetch = MODE != 1 && gtg_smem(p, MODE, 4, true) <= limit;
-    A.stall = p->test_stall;
-    A.peer_polls = p->test_stall ? p->test_polls : WAIT_POLLS;
-    A.nbuf = GTG_NBUF;
-    while (A.nbuf > 2 && gtg_smem(p, MODE, A.nbuf, A.prefetch) > limit) --A.nbuf;
-    const size_t sm = gtg_smem(p, MODE, A.nbuf, A.prefetch);
-    if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
-    // patch sides of the uv-tiles 32 and 64 with 15 x 15 tiles are compile-time constants
-    void (*kern)(GtgArgs) = p->PW == 46 ? gtg_kernel<MODE, 46> : p->PW == 78 ? gtg_kernel<MODE, 78>
-                                                                              : gtg_kernel<MODE, 0>;
+    size_t sm = 0;
+    gtg_shape(p, p->PW, p->chunk_bytes, MODE, A, sm);
+    void (*kern)(GtgArgs) = gtg_kernel_for<MODE, false>(p->PW);
     RIMO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nu, p->n_sm);
     kern<<<grid, GTG_THREADS, sm, s>>>(A);
-    if (MODE != 0 && br.m1 > br.m0)
-        merge_patches_kernel<<<br.m1 - br.m0, 256, 0, s>>>(p->d_patch, p->d_merge + br.m0, p->PW * p->PW);
+    if (MODE != 0 && br.m1 > br.m0) {
+        MergeJob mj;
+        mj.patch = p->d_patch;
+        mj.groups = p->d_merge + br.m0;
+        mj.npatch = p->PW * p->PW;
+        merge_patches_kernel<false><<<br.m1 - br.m0, 256, 0, s>>>(mj, nullptr, nullptr, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The grid step of a stage-batched apply: one persistent launch over the units of every
+// (plan, bin) job, taken heaviest first from one queue, then one merge launch.
+struct WideGtg {
+    GtgArgs A;
+    size_t sm = 0;
+    int grid = 0, merge_blocks = 0, njobs = 0, PW = 0;
+    GtgJob* jobs = nullptr;
+    int2* queue = nullptr;
+    MergeJob* mjobs = nullptr;
+    int* mfirst = nullptr;
+    int64_t units = 0;
+    ~WideGtg() {
+        cudaFree(jobs);
+        cudaFree(queue);
+        cudaFree(mjobs);
+        cudaFree(mfirst);
+    }
+};
+
+WideGtg* wide_gtg_create(const std::vector<WideJob>& jobs, cudaStream_t s) {
+    if (jobs.empty()) fail(RIMO_ERR_INVALID_ARG, "no jobs");
+    auto* w = new WideGtg();
+    try {
+        const rimo_plan* p0 = jobs[0].p;
+        int pw_max = 0, cb_max = 0;
+        bool one_pw = true;
+        for (const WideJob& j : jobs) {
+            pw_max = std::max(pw_max, j.p->PW);
+            cb_max = std::max(cb_max, j.p->chunk_bytes);
+            one_pw = one_pw && j.p->PW == p0->PW;
+        }
+        std::memset(&w->A, 0, sizeof(w->A));
+        gtg_shape(p0, pw_max, cb_max, 2, w->A, w->sm);
+        // one patch side: its compile-time kernel; several: the kernel reading each job's
+        w->PW = one_pw ? p0->PW : 0;
+        std::vector<GtgJob> gj;
+        std::vector<MergeJob> mj;
+        std::vector<int> mf{0};
+        struct Q {
+            int64_t n;
+            int job, slot;
+        };
+        std::vector<Q> q;
+        for (size_t j = 0; j < jobs.size(); ++j) {
+            const rimo_plan* p = jobs[j].p;
+            if (p->TS != p0->TS || p->gx != p0->gx || p->gy != p0->gy)
+                fail(RIMO_ERR_UNSUPPORTED, "jobs of one grid-step launch need one grid and uv-tile size");
+            const auto& br = p->bins[jobs[j].bin];
+            gj.push_back(gtg_job(p, jobs[j].bin, jobs[j].X, jobs[j].patch));
+            for (int u = 0; u < br.t1 - br.t0; ++u) {
+                const TileDesc& td = p->tiles_host[(size_t)br.t0 + u];
+                q.push_back(Q{td.ve - td.vb, (int)j, u});
+            }
+            MergeJob m;
+            m.patch = jobs[j].patch;
+            m.groups = p->d_merge + br.m0;
+            m.npatch = p->PW * p->PW;
+            mj.push_back(m);
+            mf.push_back(mf.back() + (br.m1 - br.m0));
+        }
+        // heaviest first over the whole batch (ties: job, then slot), dealt in snake order
+        std::stable_sort(q.begin(), q.end(), [](const Q& a, const Q& b) { return a.n > b.n; });
+        std::vector<int2> qq(q.size());
+        for (size_t i = 0; i < q.size(); ++i) qq[i] = make_int2(q[i].job, q[i].slot);
+        w->units = (int64_t)q.size();
+        w->njobs = (int)jobs.size();
+        w->merge_blocks = mf.back();
+        RIMO_CUDA(cudaMalloc(&w->jobs, gj.size() * sizeof(GtgJob)));
+        RIMO_CUDA(cudaMalloc(&w->queue, std::max<size_t>(1, qq.size()) * sizeof(int2)));
+        RIMO_CUDA(cudaMalloc(&w->mjobs, mj.size() * sizeof(MergeJob)));
+        RIMO_CUDA(cudaMalloc(&w->mfirst, mf.size() * sizeof(int)));
+        RIMO_CUDA(cudaMemcpyAsync(w->jobs, gj.data(), gj.size() * sizeof(GtgJob), cudaMemcpyHostToDevice, s));
+        if (!qq.empty())
+            RIMO_CUDA(cudaMemcpyAsync(w->queue, qq.data(), qq.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaMemcpyAsync(w->mjobs, mj.data(), mj.size() * sizeof(MergeJob), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaMemcpyAsync(w->mfirst, mf.data(), mf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaStreamSynchronize(s));
+        w->A.jobs = w->jobs;
+        w->A.queue = w->queue;
+        w->A.nunits = (int)q.size();
+        if ((int64_t)w->A.nunits != w->units) fail(RIMO_ERR_UNSUPPORTED, "too many work units for one launch");
+        w->grid = (int)std::min<int64_t>(w->units, p0->n_sm);
+    } catch (...) {
+        delete w;
+        throw;
+    }
+    return w;
+}
+
+void wide_gtg_destroy(WideGtg* w) { delete w; }
+
+int64_t wide_gtg_units(const WideGtg* w) { return w->units; }
+
+void wide_gtg(const WideGtg* w, cudaStream_t s) {
+    if (w->units == 0) return;
+    void (*kern)(GtgArgs) = gtg_kernel_for<2, true>(w->PW);
+    RIMO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->sm));
+    kern<<<w->grid, GTG_THREADS, w->sm, s>>>(w->A);
+    if (w->merge_blocks > 0) {
+        MergeJob none;
+        none.patch = nullptr;
+        none.groups = nullptr;
+        none.npatch = 0;
+        merge_patches_kernel<true><<<w->merge_blocks, 256, 0, s>>>(none, w->mjobs, w->mfirst, w->njobs);
+    }
 }
 
 void launch_gtg(const rimo_plan* p, int bin, int mode, const float2* y_in, float2* y_out,

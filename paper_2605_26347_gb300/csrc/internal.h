@@ -241,6 +241,40 @@ void launch_gbuild(const rimo_plan* p, cudaStream_t s);
 void launch_kwtab(const rimo_plan* p, cudaStream_t s);
 void launch_gbuild_range(const rimo_plan* p, int64_t v0, int64_t n, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Stage-batched applies (wideband batches): one (plan, w-bin) of the batch and the scratch
+// it uses; every pass of Phi^dagger Phi runs as one launch over all jobs.
+struct WideJob {
+    const rimo_plan* p;
+    int bin;
+    int group;        // the channel: index of its (x, out) image pair
+    float2* AB;       // half-transformed rows, 2 nx ny
+    float2* X;        // forward grid, then the folded gridded grid, gx gy
+    float2* patch;    // tile patches of the bin's work units, (t1 - t0) PW^2
+};
+// Job of block b of a launch over a job table: the last job whose first block is <= b
+// (first: njobs + 1 non-decreasing block offsets).
+__device__ __forceinline__ int job_of(const int* first, int njobs, int b) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+struct WideFft;   // device job tables of the transform passes (fft.cu)
+struct WideGtg;   // device unit queue of the grid step (grid.cu)
+WideFft* wide_fft_create(const std::vector<WideJob>& jobs, const std::vector<const float2*>& x,
+                         const std::vector<float2*>& out, cudaStream_t s);
+void wide_fft_destroy(WideFft* w);
+void wide_fwd(const WideFft* w, cudaStream_t s);                 // F Z_p of every job
+void wide_inv(const WideFft* w, int real_only, cudaStream_t s);  // fold, Z_p^H F^H, Sigma_p per channel
+WideGtg* wide_gtg_create(const std::vector<WideJob>& jobs, cudaStream_t s);
+void wide_gtg_destroy(WideGtg* w);
+int64_t wide_gtg_units(const WideGtg* w);
+void wide_gtg(const WideGtg* w, cudaStream_t s);  // G_p^H G_p of every job: one persistent launch
+
 // The three applies on stream s (defined in apply.cu).
 void apply_phi(rimo_plan* p, const float2* x, float2* y, cudaStream_t s);
 void apply_phi_adj(rimo_plan* p, const float2* y, float2* x, cudaStream_t s);

@@ -93,6 +93,7 @@ void validate_params(const rimo_plan_params& q) {
     if (q.tile_size != 0 && q.tile_size != 32 && q.tile_size != 64) bad("tile_size must be 0, 32 or 64");
     if (q.wkernel_table != 0 && (q.wkernel_table < 16 || q.wkernel_table > (1 << 22)))
         bad("wkernel_table must be 0 or in [16, 2^22]");
+    if (q.uv_order < 0 || q.uv_order > 2) bad("uv_order must be 0, 1 or 2");
     if (q.kb_beta < 0) bad("kb_beta must be >= 0");
 }
 
@@ -376,13 +377,19 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
             // that the GTG_CHUNK consecutive visibilities of one ring chunk, de-gridded and
             // gridded at the same time by as many warps, come from far-apart instants and
             // rarely update the same grid cells.
-            {
+            // (uv_order 0; 1 keeps the time order; 2 orders the tile's visibilities by a
+            // SplitMix64 hash of their index)
+            if (q.uv_order == 0) {
                 const int64_t n = x.ve - x.vb, nc = (n + GTG_CHUNK - 1) / GTG_CHUNK;
                 tmp.assign(order.begin() + x.vb, order.begin() + x.ve);
                 int64_t o = x.vb;
                 for (int64_t c = 0; c < nc; ++c)
                     for (int64_t r = 0; r < GTG_CHUNK; ++r)
                         if (r * nc + c < n) order[o++] = tmp[r * nc + c];
+            } else if (q.uv_order == 2) {
+                std::stable_sort(order.begin() + x.vb, order.begin() + x.ve, [](int32_t a, int32_t b) {
+                    return planner::splitmix64((uint64_t)a) < planner::splitmix64((uint64_t)b);
+                });
             }
             x.bytes = 0;
             for (int64_t i = x.vb; i < x.ve; ++i) {

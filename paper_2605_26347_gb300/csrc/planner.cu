@@ -44,13 +44,6 @@ void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f, int
     for (auto& t : th) t.join();
 }
 
-// SplitMix64 output function (Steele, Lea & Flood 2014).
-static inline uint64_t splitmix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 std::vector<double> subset_w(const double* uvw, int64_t M, uint64_t seed, double fraction) {
     double frac = std::max(fraction, std::min(1.0, 4096.0 / (double)std::max<int64_t>(M, 1)));
     std::vector<double> out;

@@ -12,6 +12,13 @@ namespace rimo {
 namespace planner {
 
 constexpr int N_SUPPORT_BINS = 64;
+
+// SplitMix64 output function (Steele, Lea & Flood 2014).
+inline uint64_t splitmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 constexpr int META_BYTES_PER_VIS = 16;
 
 struct KernelGeom {

@@ -24,7 +24,7 @@ def oracle_params(nx, ny, fov_x, fov_y, **kw) -> opl.PlanParams:
     for k, v in kw.items():
         if k == "n_weight":
             args["div_n"] = bool(v)
-        elif k in ("tile_size", "block_bytes_max"):
+        elif k in ("tile_size", "block_bytes_max", "uv_order"):
             continue
         elif k == "taper_literal":
             args["taper_literal"] = bool(v)

@@ -14,7 +14,9 @@ the whole vector or image, tolerance 1e-5 for complex FP32 against FP64):
 * 2048^2, FoV 2.5 deg, 16 w-bins, Phi^dagger Phi through H_p = G_p^dagger G_p (Section 3.3)
   and through G^dagger G before H is built;
 * 1024^2 wideband: three channels (0.9, 1.29, 1.7 GHz; 4, 18 and 32 w-bins) batched in one
-  graph launch against the oracle of each channel.
+  graph launch, staged (one launch per pass over every channel and bin, the grid step one
+  persistent launch over all their work units) and as branches, against the oracle of
+  each channel.
 """
 import math
 import os
@@ -166,17 +168,20 @@ def test_c4_three_channels_batched():
         uvw = np.ascontiguousarray(uvw_c[np.sort(rng.choice(uvw_c.shape[0], 150_000, replace=False))])
         nb = int(round(4 + 28 * c / 31))
         kw = dict(n_wbins=nb)
-        plans.append(pkg.Plan(uvw, pkg.default_params(1024, 1024, fov, fov, tile_size=64 if c == 15 else 0, **kw)))
+        plans.append(pkg.Plan(uvw, pkg.default_params(1024, 1024, fov, fov, tile_size=64, **kw)))
         oplan = opl.make_plan(uvw, opl.PlanParams(nx=1024, ny=1024, fov_x=fov, fov_y=fov, **kw))
         ops.append(oop.Operator(uvw, oplan, workers=WORKERS))
         assert_same_plan(plans[-1], ops[-1])
         xs.append(synth.make_sky(1024, 2004 + c))
     assert [p.info()["P"] for p in plans] == [4, 18, 32]
-    batch = pkg.Batch(plans)
     x = np.stack(xs)
-    out = to_host(batch.phi_adj_phi(torch.from_numpy(x).cuda()))
-    for i, op in enumerate(ops):
-        assert rel(out[i], op.phi_adj_phi(x[i].astype(np.complex128))) < TOL
-    batch.close()
+    refs = [op.phi_adj_phi(x[i].astype(np.complex128)) for i, op in enumerate(ops)]
+    for form in (pkg.BATCH_STAGED, pkg.BATCH_BRANCHES):
+        batch = pkg.Batch(plans, form=form)
+        assert batch.layout()["staged"] == (form == pkg.BATCH_STAGED)
+        out = to_host(batch.phi_adj_phi(torch.from_numpy(x).cuda()))
+        for i in range(len(ops)):
+            assert rel(out[i], refs[i]) < TOL, (form, i)
+        batch.close()
     for p in plans:
         p.close()
