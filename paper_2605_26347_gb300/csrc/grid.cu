@@ -86,6 +86,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr int GTG_CONSUMERS = GTG_CHUNK;                 // consumer warps
 constexpr int GTG_THREADS = (GTG_CONSUMERS + 1) * 32;   // + one producer warp
 constexpr int GTG_NBUF = 4;   // maximum depth of the tap ring (the plan may use fewer)
+constexpr int GTG_NX = 3;     // maximum number of X patch buffers (prefetch NX - 1 units ahead)
 constexpr int GTG_HDR = 256;  // shared-memory header: the ring's and the X buffers' mbarriers
 constexpr int GTG_CV = GTG_CHUNK;  // visibilities per chunk (one per consumer warp)
 
@@ -115,7 +116,8 @@ struct GtgArgs {
     int chunk_bytes;
     int nbuf;               // ring depth in use, 2..GTG_NBUF
     int ntv, shift;
-    int prefetch;           // the producer bulk-copies the next unit's X patch (double buffer)
+    int prefetch;           // the producer bulk-copies the X patches of the next units
+    int xbufs;              // X patch buffers with prefetch (2 or 3: 1 or 2 units ahead)
     // failure-detection test (rimo_plan_set_wait_test): the consumers withhold their release
     // of ring slots, and the producer's waits on the consumers give up after peer_polls
     int stall;
@@ -288,8 +290,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
     uint64_t* empty = full + GTG_NBUF;
-    uint64_t* xfull = empty + GTG_NBUF;  // [2] X patch buffer landed
-    uint64_t* xfree = xfull + 2;         // [2] consumers are done with the buffer
+    uint64_t* xfull = empty + GTG_NBUF;  // [GTG_NX] X patch buffer landed
+    uint64_t* xfree = xfull + GTG_NX;    // [GTG_NX] consumers are done with the buffer
     VisMeta* mring = reinterpret_cast<VisMeta*>(smraw + GTG_HDR);      // GTG_NBUF x GTG_CV entries
     float2* taps = reinterpret_cast<float2*>(smraw + GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta));
     // shared memory laid out for the launch's largest patch (a staged batch's jobs may have
@@ -298,9 +300,9 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
     const int chunk_f2 = A.chunk_bytes / 8;
     const uint32_t NB = (uint32_t)A.nbuf;
     const bool pre = GATHER && A.prefetch;
+    const int NX = pre ? A.xbufs : 1;  // X patch buffers
     float2* Xbuf0 = taps + (size_t)NB * chunk_f2;
-    float2* Xbuf1 = Xbuf0 + (pre ? npmax : 0);
-    int* Ahi = reinterpret_cast<int*>(Xbuf1 + (GATHER ? npmax : 0));  // [cell][re, im] words
+    int* Ahi = reinterpret_cast<int*>(Xbuf0 + (GATHER ? (size_t)NX * npmax : 0));  // [cell][re, im] words
     int* Alo = Ahi + (SCATTER ? 2 * npmax : 0);
     __shared__ volatile int s_abort;
     __shared__ float s_xmax[GTG_CONSUMERS];
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], GTG_CONSUMERS);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < GTG_NX; ++b) {
             mbar_init(&xfull[b], 1);
             mbar_init(&xfree[b], GTG_CONSUMERS);
         }
@@ -325,6 +327,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
         uint32_t g = 0;
+        int xq = 0;  // the next unit whose X patch is to be copied
         for (int r = 0;; ++r) {
             const int idx = unit_of(r, cb, G);
             if (idx >= A.nunits) break;
@@ -332,32 +335,42 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
             const GtgJob* J = unit_job<TABLE>(A, idx, slot);
             const TileDesc td = J->units[slot];
             const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
-            const int PW = PWC > 0 ? PWC : (TABLE ? J->PW : A.PW), npatch = PW * PW;
-            if (pre) {
-                // X patch of this unit into buffer r & 1, once the consumers released it
-                // (unit r - 2); rows wrap along u, a row past the last column splits in two
-                const int j = r & 1;
-                if (r >= 2 && !s_abort && !mbar_wait_bounded(&xfree[j], ((r >> 1) - 1) & 1, A.peer_polls)) {
+            // X patches of units r .. r + NX - 2 (buffer q % NX, once the consumers released
+            // it after unit q - NX); rows wrap along u, a row past the last column splits in two
+            while (pre && xq <= r + NX - 2) {
+                const int iq = unit_of(xq, cb, G);
+                if (iq >= A.nunits) break;
+                const int j = xq % NX;
+                if (xq >= NX && !s_abort &&
+                    !mbar_wait_bounded(&xfree[j], ((xq / NX) - 1) & 1, A.peer_polls)) {
                     s_abort = 1;
                     atomicExch(J->status, 1);
                 }
-                if (s_abort) {
-                    for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
-                        (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
-                    if (r >= 1) (void)mbar_wait_bounded(&xfull[(r - 1) & 1], ((r - 1) >> 1) & 1);
-                    return;
-                }
-                float2* dst = j ? Xbuf1 : Xbuf0;
-                const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
+                if (s_abort) break;
+                int sq;
+                const GtgJob* Jq = unit_job<TABLE>(A, iq, sq);
+                const TileDesc tq = Jq->units[sq];
+                const int PW = PWC > 0 ? PWC : (TABLE ? Jq->PW : A.PW), npatch = PW * PW;
+                float2* dst = Xbuf0 + (size_t)j * npmax;
+                const int u0 = tq.tu * A.TS, v0 = tq.tv * A.TS;
                 const int n1 = (v0 + PW <= A.gy) ? PW : A.gy - v0;  // cells before the wrap
                 mbar_arrive_expect_tx(&xfull[j], (uint32_t)(npatch * sizeof(float2)));
                 for (int a = 0; a < PW; ++a) {
                     int gu = u0 + a;
                     if (gu >= A.gx) gu -= A.gx;
-                    const float2* row = J->X + (size_t)gu * A.gy;
+                    const float2* row = Jq->X + (size_t)gu * A.gy;
                     bulk_g2s(dst + a * PW, row + v0, (uint32_t)(n1 * sizeof(float2)), &xfull[j]);
                     if (n1 < PW) bulk_g2s(dst + a * PW + n1, row, (uint32_t)((PW - n1) * sizeof(float2)), &xfull[j]);
                 }
+                ++xq;
+            }
+            if (s_abort) {
+                // let the copies already in flight land before the block may exit
+                for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
+                    (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
+                for (int q = (xq > NX ? xq - NX : 0); q < xq; ++q)
+                    (void)mbar_wait_bounded(&xfull[q % NX], (q / NX) & 1);
+                return;
             }
             for (int c = 0; c < nchunks; ++c, ++g) {
                 const ChunkDesc cd = J->chunks[td.cb + c];
@@ -372,7 +385,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
                     // let the copies already in flight land before the block may exit
                     for (uint32_t q = (g > NB ? g - NB : 0); q < g; ++q)
                         (void)mbar_wait_bounded(&full[q % NB], (q / NB) & 1);
-                    if (pre) (void)mbar_wait_bounded(&xfull[r & 1], (r >> 1) & 1);
+                    for (int q = (xq > NX ? xq - NX : 0); q < xq; ++q)
+                        (void)mbar_wait_bounded(&xfull[q % NX], (q / NX) & 1);
                     return;
                 }
                 mbar_arrive_expect_tx(&full[b], cd.bytes + nv * (uint32_t)sizeof(VisMeta));
@@ -395,8 +409,8 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
         const int PW = PWC > 0 ? PWC : (TABLE ? J->PW : A.PW), npatch = PW * PW;
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
         float xm = 0.f;
-        float2* Xs = (r & 1) && pre ? Xbuf1 : Xbuf0;
-        if (pre && !s_abort && !mbar_wait_or_abort(&xfull[r & 1], (r >> 1) & 1, &s_abort)) {
+        float2* Xs = Xbuf0 + (pre ? (size_t)(r % NX) * npmax : 0);
+        if (pre && !s_abort && !mbar_wait_or_abort(&xfull[r % NX], (r / NX) & 1, &s_abort)) {
             s_abort = 1;
             atomicExch(J->status, 1);
         }
@@ -467,7 +481,7 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
         }
         if (pre) {
             __syncwarp();
-            if (lane == 0) mbar_arrive(&xfree[r & 1]);
+            if (lane == 0) mbar_arrive(&xfree[r % NX]);
         }
         consumers_sync();
         if (SCATTER && !s_abort) {
@@ -517,10 +531,11 @@ __global__ void __launch_bounds__(256) merge_patches_kernel(const __grid_constan
     }
 }
 
-static size_t gtg_smem_dims(int PW, int chunk_bytes, int mode, int nbuf, bool prefetch) {
+static size_t gtg_smem_dims(int PW, int chunk_bytes, int mode, int nbuf, bool prefetch, int xbufs = 2) {
     const size_t npatch = (size_t)PW * PW * sizeof(float2);
-    // X patch (float2; two when prefetched) when de-gridding, hi + lo words (2 x int2) when gridding
-    const int nx = mode != 1 ? (prefetch ? 2 : 1) : 0;
+    // X patches (float2; xbufs of them when prefetched) when de-gridding, hi + lo words
+    // (2 x int2) when gridding
+    const int nx = mode != 1 ? (prefetch ? xbufs : 1) : 0;
     return GTG_HDR + GTG_NBUF * GTG_CV * sizeof(VisMeta) + (size_t)nbuf * chunk_bytes +
            (size_t)(nx + (mode != 0 ? 2 : 0)) * npatch;
 }
@@ -529,15 +544,24 @@ size_t gtg_smem(const rimo_plan* p, int mode, int nbuf, bool prefetch) {
     return gtg_smem_dims(p->PW, p->chunk_bytes, mode, nbuf, prefetch);
 }
 
-// Launch shape of the grid step for a patch side and tap-ring chunk (prefetch, ring
-// depth, shared memory); `mode` as in launch_gtg.
-static void gtg_shape(const rimo_plan* p, int PW, int chunk_bytes, int mode, GtgArgs& A, size_t& sm) {
+// Launch shape of the grid step for a patch side and tap-ring chunk (prefetch, X buffers,
+// ring depth, shared memory); `mode` as in launch_gtg.  Units of a few chunks (mean below
+// 8 chunks of visibilities) leave too little time between two X patch copies for one copy
+// ahead to land: they get a third X buffer, two units ahead, at the price of a ring slot.
+static void gtg_shape(const rimo_plan* p, int PW, int chunk_bytes, int mode, double vis_per_unit, GtgArgs& A,
+                      size_t& sm) {
     const size_t limit = 227 * 1024 - 2048;  // minus the kernel's static shared memory
-    // prefetch the X patches when a double buffer still leaves a GTG_NBUF-deep tap ring
-    A.prefetch = mode != 1 && gtg_smem_dims(PW, chunk_bytes, mode, 4, true) <= limit;
+    A.xbufs = vis_per_unit < 8.0 * GTG_CV ? GTG_NX : 2;
+    // prefetch the X patches when the buffers still leave a 3-deep tap ring (4-deep with two)
+    const int ring = A.xbufs == 2 ? GTG_NBUF : GTG_NBUF - 1;
+    A.prefetch = mode != 1 && gtg_smem_dims(PW, chunk_bytes, mode, ring, true, A.xbufs) <= limit;
+    if (mode != 1 && !A.prefetch && A.xbufs > 2) {
+        A.xbufs = 2;
+        A.prefetch = gtg_smem_dims(PW, chunk_bytes, mode, GTG_NBUF, true, 2) <= limit;
+    }
     A.nbuf = GTG_NBUF;
-    while (A.nbuf > 2 && gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch) > limit) --A.nbuf;
-    sm = gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch);
+    while (A.nbuf > 2 && gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch, A.xbufs) > limit) --A.nbuf;
+    sm = gtg_smem_dims(PW, chunk_bytes, mode, A.nbuf, A.prefetch, A.xbufs);
     if (sm > limit) fail(RIMO_ERR_UNSUPPORTED, "tile patch and tap ring exceed shared memory");
     A.gx = p->gx;
     A.gy = p->gy;
@@ -585,7 +609,7 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.y_in = y_in;
     A.y_out = y_out;
     size_t sm = 0;
-    gtg_shape(p, p->PW, p->chunk_bytes, MODE, A, sm);
+    gtg_shape(p, p->PW, p->chunk_bytes, MODE, (double)(br.ve - br.vb) / nu, A, sm);
     void (*kern)(GtgArgs) = gtg_kernel_for<MODE, false>(p->PW);
     RIMO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nu, p->n_sm);
@@ -631,8 +655,13 @@ WideGtg* wide_gtg_create(const std::vector<WideJob>& jobs, cudaStream_t s) {
             cb_max = std::max(cb_max, j.p->chunk_bytes);
             one_pw = one_pw && j.p->PW == p0->PW;
         }
+        int64_t nvis = 0, nun = 0;
+        for (const WideJob& j : jobs) {
+            nvis += j.p->bins[j.bin].ve - j.p->bins[j.bin].vb;
+            nun += j.p->bins[j.bin].t1 - j.p->bins[j.bin].t0;
+        }
         std::memset(&w->A, 0, sizeof(w->A));
-        gtg_shape(p0, pw_max, cb_max, 2, w->A, w->sm);
+        gtg_shape(p0, pw_max, cb_max, 2, (double)nvis / std::max<int64_t>(1, nun), w->A, w->sm);
         // one patch side: its compile-time kernel; several: the kernel reading each job's
         w->PW = one_pw ? p0->PW : 0;
         std::vector<GtgJob> gj;

@@ -20,15 +20,19 @@ pytestmark = pytest.mark.gpu
 TIMEOUT = 5
 
 
-def test_bounded_wait_runs_out_then_the_plan_recovers():
+@pytest.mark.parametrize("n, m, fov_deg", [
+    # 128^2, 20k visibilities, one w-bin: a few dozen uv-tiles of ~300 visibilities, so every
+    # block of the grid step streams more tap chunks than its ring holds (two X buffers)
+    (128, 20000, 2.0),
+    # 512^2, 60k visibilities: units of a few chunks (three X buffers, two units ahead)
+    (512, 60000, 2.0),
+])
+def test_bounded_wait_runs_out_then_the_plan_recovers(n, m, fov_deg):
     import torch
 
     import paper_2605_26347_gb300 as pkg
-    # 128^2 image, 20k visibilities, one w-bin: a few dozen uv-tiles of ~300 visibilities,
-    # so every block of the grid step streams more tap chunks than its ring holds
-    n = 128
-    fov = math.radians(2.0)
-    uvw = synth.make_uvw(20000, 60, 1.28e9, 4242)
+    fov = math.radians(fov_deg)
+    uvw = synth.make_uvw(m, 60, 1.28e9, 4242)
     plan = pkg.Plan(uvw, pkg.default_params(n, n, fov, fov, n_wbins=1))
     x = to_dev(synth.make_sky(n, 4243))
     before = to_host(plan.phi_adj_phi(x))
