@@ -37,6 +37,15 @@ def test_training_reduces_the_loss(trained):
     assert sur.w_scale > 0
 
 
+@pytest.mark.xfail(strict=True, reason="the 1e-4 target of the surrogate path is not met: a 128-wide last hidden "
+                   "layer cannot span the exact tiles to 1e-4 (tests/test_surrogate_rank_bound.py), and the "
+                   "trained network stays near 1e-2 here (6.5e-3 at the 4096^2 / 50M workload)")
+def test_surrogate_path_within_1e4_of_the_exact_path(trained):
+    _, exact, _, splan, _ = trained
+    x = to_dev(trained[0].sky)
+    assert rel(to_host(splan.phi_adj_phi(x)), to_host(exact.phi_adj_phi(x))) <= 1e-4
+
+
 def test_surrogate_path_beats_the_method_without_w_kernels(trained):
     import paper_2605_26347_gb300 as pkg
     w, exact, _, splan, _ = trained
