@@ -155,9 +155,9 @@ typedef struct rimo_plan_info {
                                /* than max_wsupport taps to keep w_norm_frac         */
     int32_t weighted;          /* 1: a data weighting is injected (set_weights)    */
     /* Holographic matrices (0 until rimo_build_holographic has run; Section 3.3): */
-    int64_t h_entries;         /* stored entries: covered owner cells x entries per  */
-                               /* owner row, each unordered pair of cells once       */
-    int64_t h_nonzero;         /* stored entries that are not zero (cell pairs that  */
+    int64_t h_entries;         /* dense stencil entries: covered owner cells x       */
+                               /* entries per owner row (each cell pair once)        */
+    int64_t h_nonzero;         /* entries stored: the non-zero ones (cell pairs that */
                                /* some visibility's footprint covers together)       */
     int64_t h_nnz;             /* non-zeros of the full Hermitian H_p = G_p^H G_p,   */
                                /* summed over bins: both triangles and the diagonal  */
@@ -301,9 +301,11 @@ rimo_status rimo_apply_phi_adj_phi(rimo_plan_t plan, const rimo_cfloat* x_dev,
  * plan's tiles.  A stored-G plan builds H from G; a holographic or on-the-fly plan generates
  * each bin's exact tiles for its build, so all of G is never held (Fig. 2, regime b).
  * H_p is Hermitian and stored once per cell pair: every grid cell that some visibility
- * footprint covers gets a row of (H+1)^2 + H^2 complex entries, H = S_max - 1 (421 for
- * S_max = 15), so it pays off where visibilities per covered cell are many.  Fails with
- * BUDGET (before allocating the rows) when mem_budget_bytes is set and G plus H would
+ * footprint covers owns a row over the (H+1)^2 + H^2 pairs it can lead (H = S_max - 1: 421
+ * for S_max = 15), of which only the non-zero entries are kept (complex value + 16-bit
+ * entry number, rows found by offsets), so it pays off where visibilities per covered
+ * cell are many.  Built bin by bin through a temporary of the bin's dense rows.  Fails
+ * with BUDGET (releasing what it built) when mem_budget_bytes is set and G plus H would
  * exceed it.  A second call does nothing.  info.h_bytes reports the rows and patches.
  * Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OOM, BUDGET, CUDA.
  */

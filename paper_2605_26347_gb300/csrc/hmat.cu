@@ -13,7 +13,11 @@
 //
 // Only owners that some footprint covers get a row: a coverage pass marks the covered
 // cells of each needed tile (bitmap), the host turns the counts into row offsets, and the
-// build pass writes the rows.  Build: one CTA per 4 x 4 block of owners, one warp per
+// build pass writes the rows.  Where cells see one or a few visibilities most pairs are
+// never covered together, so a bin's rows keep only their non-zero entries (value and entry
+// number, rows found by offsets) when that is smaller than the dense rows: the build writes
+// the bin's rows densely to a temporary, a count pass decides, and a compaction pass keeps
+// each row's non-zero values; a bin of dense coverage keeps the dense rows as they are.  Build: one CTA per 4 x 4 block of owners, one warp per
 // owner keeping its entries in shared memory (no atomics); the candidate visibilities
 // (anchor within D before the block) come from an anchor index sorted by (g0, h0) that the
 // host prepares.  Apply: one CTA per needed tile, one warp per owner; the gathered sum
@@ -295,7 +299,9 @@ struct HApplyArgs {
     const int32_t* need;      // needed tiles of the bin
     const uint32_t* bits;
     const int64_t* hoff;
-    const float2* rows;
+    const float2* val;        // the owner rows: dense [owner][ne], or their non-zero entries
+    const uint16_t* idx;      // compressed: the entry numbers
+    const int64_t* roff;      // compressed: [owner + 1] first entry of each owner row (null: dense)
     const uint32_t* tmax;     // [needed tile] max |h|_1 of the tile's rows
     const int32_t* ent;
     float2* patch;            // [needed tile][PW * PW]
@@ -378,11 +384,14 @@ __global__ void __launch_bounds__(HA_WARPS * 32, 1) happly_kernel(HApplyArgs A) 
             if ((tbits[cell >> 5] >> (cell & 31)) & 1u) ++rank;
         }
         const int lu = cell / A.TS, lv = cell - lu * A.TS;
-        const float2* row = A.rows + (size_t)(base + k) * ne;
+        const bool dense = A.roff == nullptr;
+        const int64_t q0 = dense ? (base + k) * ne : __ldg(&A.roff[base + k]);
+        const int64_t q1 = dense ? q0 + ne : __ldg(&A.roff[base + k + 1]);
         const float2 zo = Z[lu * PW + lv];
         float gx = 0.f, gy = 0.f;
-        for (int e = lane; e < ne; e += 32) {
-            const float2 h = __ldg(&row[e]);
+        for (int64_t q = q0 + lane; q < q1; q += 32) {
+            const float2 h = __ldg(&A.val[q]);
+            const int e = dense ? (int)(q - q0) : __ldg(&A.idx[q]);
             const int en = sent[e];
             const int a = (en >> 8) & 255, b = en & 255;
             if ((en >> 16) == 0) {
@@ -437,25 +446,49 @@ struct DevBuf {
     ~DevBuf() { cudaFree(p); }
 };
 
-// Non-zero stored entries of a bin's owner rows: counts[0] += all, counts[1] += the
-// diagonal ones (entry 0 of a row is H[o][o]).
-__global__ void __launch_bounds__(256) hcount_kernel(const float2* __restrict__ rows, int64_t n, int ne,
-                                                     unsigned long long* counts) {
-    unsigned long long nz = 0, nd = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const float2 h = rows[e];
-        const bool on = h.x != 0.f || h.y != 0.f;
-        nz += on;
-        nd += on && (e % ne) == 0;
+// Non-zero entries of each dense owner row (one warp per row); diag[0] += the rows whose
+// entry 0 (H[o][o]) is non-zero.
+__global__ void __launch_bounds__(256) hrowcount_kernel(const float2* __restrict__ rows, int64_t nown, int ne,
+                                                        int32_t* __restrict__ counts, unsigned long long* diag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nown) return;
+    const float2* row = rows + (size_t)r * ne;
+    int n = 0;
+    for (int e = lane; e < ne; e += 32) {
+        const float2 h = row[e];
+        n += (h.x != 0.f || h.y != 0.f) ? 1 : 0;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) {
+        counts[r] = n;
+        const float2 h0 = row[0];
+        if (h0.x != 0.f || h0.y != 0.f) atomicAdd(diag, 1ull);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(counts, nz);
-        atomicAdd(counts + 1, nd);
+}
+
+// Keeps the non-zero entries of each dense owner row at roff[row] (one warp per row,
+// entries in row order).
+__global__ void __launch_bounds__(256) hcompact_kernel(const float2* __restrict__ rows, int64_t nown, int ne,
+                                                       const int64_t* __restrict__ roff, float2* __restrict__ val,
+                                                       uint16_t* __restrict__ idx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nown) return;
+    const float2* row = rows + (size_t)r * ne;
+    int64_t q = roff[r];
+    for (int e0 = 0; e0 < ne; e0 += 32) {
+        const int e = e0 + lane;
+        const float2 h = e < ne ? row[e] : make_float2(0.f, 0.f);
+        const bool on = h.x != 0.f || h.y != 0.f;
+        const uint32_t m = __ballot_sync(0xffffffffu, on);
+        if (on) {
+            const int64_t at = q + __popc(m & ((1u << lane) - 1u));
+            val[at] = h;
+            idx[at] = (uint16_t)e;
+        }
+        q += __popc(m);
     }
 }
 
@@ -473,7 +506,9 @@ void launch_happly(const rimo_plan* p, int bin, cudaStream_t s) {
     A.need = p->d_need_list + br.n0;
     A.bits = p->d_hbits[bin];
     A.hoff = p->d_hoff[bin];
-    A.rows = p->d_hrows[bin];
+    A.val = p->d_hval[bin];
+    A.idx = p->h_dense[bin] ? nullptr : p->d_hidx[bin];
+    A.roff = p->h_dense[bin] ? nullptr : p->d_hroff[bin];
     A.tmax = p->d_htmax[bin];
     A.ent = p->d_hent;
     A.patch = p->d_hpatch;
@@ -553,7 +588,10 @@ static void build_holographic(rimo_plan* p, cudaStream_t s) {
     p->d_hslot = upload_vec(p, hslot, s);
     p->d_hbits.assign(P, nullptr);
     p->d_hoff.assign(P, nullptr);
-    p->d_hrows.assign(P, nullptr);
+    p->d_hval.assign(P, nullptr);
+    p->d_hidx.assign(P, nullptr);
+    p->d_hroff.assign(P, nullptr);
+    p->h_dense.assign(P, 0);
     p->d_htmax.assign(P, nullptr);
     p->hoff_host.assign(P, {});
     int max_need = 1;
@@ -597,59 +635,117 @@ static void build_holographic(rimo_plan* p, cudaStream_t s) {
         total += p->hoff_host[b][nneed];
         p->d_hoff[b] = upload_vec(p, p->hoff_host[b], s);
     }
-    const int64_t h_bytes = total * ne * (int64_t)sizeof(float2);
     const size_t patch_bytes = (size_t)max_need * p->PW * p->PW * sizeof(float2);
-    if (p->prm.mem_budget_bytes > 0 && p->info.g_bytes + h_bytes > p->prm.mem_budget_bytes)
-        fail(RIMO_ERR_BUDGET, "holographic matrices need " + std::to_string(h_bytes) + " bytes beyond G");
     p->d_hpatch = (float2*)dev_alloc(p, patch_bytes);
     const size_t sm = hbuild_smem(ne, p->max_S, D);
     if (sm > 227 * 1024) fail(RIMO_ERR_UNSUPPORTED, "holographic build: owner rows exceed shared memory");
     RIMO_CUDA(cudaFuncSetAttribute(hbuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int per_tile = (TS / HB_OWN) * (TS / HB_OWN);
-    for (int b = 0; b < P; ++b) {
-        const int nneed = p->bins[b].n1 - p->bins[b].n0;
-        const int64_t nown = p->hoff_host[b][(size_t)nneed];
-        p->d_hrows[b] = (float2*)dev_alloc(p, (size_t)std::max<int64_t>(1, nown) * ne * sizeof(float2));
-        p->d_htmax[b] = (uint32_t*)dev_alloc(p, (size_t)std::max(1, nneed) * sizeof(uint32_t));
-        RIMO_CUDA(cudaMemsetAsync(p->d_htmax[b], 0, (size_t)std::max(1, nneed) * sizeof(uint32_t), s));
-        if (nneed == 0) continue;
-        A.arow = ai.row + (size_t)b * (gx + 1);
-        A.need = p->d_need_list + p->bins[b].n0;
-        A.bits = p->d_hbits[b];
-        A.hoff = p->d_hoff[b];
-        A.rows = p->d_hrows[b];
-        A.tmax = p->d_htmax[b];
-        // without stored G, the bin's exact tiles are generated into the tap scratch first
-        if (p->mode != RIMO_MODE_STORED_G) launch_gbuild_range(p, p->bins[b].vb, p->bins[b].ve - p->bins[b].vb, s);
-        hbuild_kernel<<<nneed * per_tile, HB_WARPS * 32, sm, s>>>(A, p->max_S);
-        RIMO_CUDA(cudaGetLastError());
-    }
-    RIMO_CUDA(cudaStreamSynchronize(s));
-    {
-        // fill of the stored rows: how many entries the footprints actually couple
-        unsigned long long* cnt = nullptr;
-        RIMO_CUDA(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
-        unsigned long long h[2] = {0, 0};
-        try {
-            RIMO_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
-            for (int b = 0; b < P; ++b) {
-                const int nneed = p->bins[b].n1 - p->bins[b].n0;
-                const int64_t n = p->hoff_host[b][(size_t)nneed] * ne;
-                if (n == 0) continue;
-                const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)p->n_sm);
-                hcount_kernel<<<blocks, 256, 0, s>>>(p->d_hrows[b], n, ne, cnt);
-            }
-            RIMO_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
-            RIMO_CUDA(cudaStreamSynchronize(s));
-        } catch (...) {
-            cudaFree(cnt);
-            throw;
+    // bin by bin: dense rows into a temporary, then only their non-zero entries kept
+    std::vector<void*> made;  // the compressed arrays, released again if the budget refuses
+    auto keep = [&](size_t bytes) {
+        void* q = dev_alloc(p, std::max<size_t>(bytes, 16));
+        made.push_back(q);
+        return q;
+    };
+    auto release_made = [&]() {
+        for (void* q : made) {
+            if (!q) continue;
+            auto it = std::find(p->owned.begin(), p->owned.end(), q);
+            if (it != p->owned.end()) p->owned.erase(it);
+            cudaFree(q);
         }
-        cudaFree(cnt);
-        p->info.h_entries = total * ne;
-        p->info.h_nonzero = (int64_t)h[0];
-        p->info.h_nnz = 2 * (int64_t)(h[0] - h[1]) + (int64_t)h[1];
+        made.clear();
+    };
+    int64_t nnz = 0, h_bytes = 0;
+    unsigned long long diag = 0;
+    DevBuf dcount, ddiag;
+    RIMO_CUDA(cudaMalloc(&ddiag.p, sizeof(unsigned long long)));
+    RIMO_CUDA(cudaMemsetAsync(ddiag.p, 0, sizeof(unsigned long long), s));
+    try {
+        for (int b = 0; b < P; ++b) {
+            const int nneed = p->bins[b].n1 - p->bins[b].n0;
+            const int64_t nown = p->hoff_host[b][(size_t)nneed];
+            p->d_htmax[b] = (uint32_t*)keep((size_t)std::max(1, nneed) * sizeof(uint32_t));
+            RIMO_CUDA(cudaMemsetAsync(p->d_htmax[b], 0, (size_t)std::max(1, nneed) * sizeof(uint32_t), s));
+            std::vector<int64_t> roff((size_t)nown + 1, 0);
+            if (nown > 0) {
+                DevBuf dense;
+                if (cudaMalloc(&dense.p, (size_t)nown * ne * sizeof(float2)) != cudaSuccess) {
+                    cudaGetLastError();
+                    fail(RIMO_ERR_OOM, "holographic build: dense rows of one bin");
+                }
+                made.push_back(nullptr);  // placeholder: the dense rows may be kept
+                A.arow = ai.row + (size_t)b * (gx + 1);
+                A.need = p->d_need_list + p->bins[b].n0;
+                A.bits = p->d_hbits[b];
+                A.hoff = p->d_hoff[b];
+                A.rows = (float2*)dense.p;
+                A.tmax = p->d_htmax[b];
+                // without stored G, the bin's exact tiles are generated into the tap scratch first
+                if (p->mode != RIMO_MODE_STORED_G)
+                    launch_gbuild_range(p, p->bins[b].vb, p->bins[b].ve - p->bins[b].vb, s);
+                hbuild_kernel<<<nneed * per_tile, HB_WARPS * 32, sm, s>>>(A, p->max_S);
+                RIMO_CUDA(cudaGetLastError());
+                cudaFree(dcount.p);
+                dcount.p = nullptr;
+                RIMO_CUDA(cudaMalloc(&dcount.p, (size_t)nown * sizeof(int32_t)));
+                const int64_t blocks = (nown * 32 + 255) / 256;
+                hrowcount_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2*)dense.p, nown, ne, (int32_t*)dcount.p,
+                                                                  (unsigned long long*)ddiag.p);
+                RIMO_CUDA(cudaGetLastError());
+                std::vector<int32_t> c((size_t)nown);
+                RIMO_CUDA(cudaMemcpyAsync(c.data(), dcount.p, c.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                RIMO_CUDA(cudaStreamSynchronize(s));
+                for (int64_t k = 0; k < nown; ++k) roff[(size_t)k + 1] = roff[(size_t)k] + c[(size_t)k];
+                const int64_t nb = roff[(size_t)nown];
+                const int64_t dense_bytes = nown * ne * (int64_t)sizeof(float2);
+                const int64_t packed_bytes =
+                    nb * (int64_t)(sizeof(float2) + sizeof(uint16_t)) + (nown + 1) * (int64_t)sizeof(int64_t);
+                const bool keep_dense = dense_bytes <= packed_bytes;
+                h_bytes += keep_dense ? dense_bytes : packed_bytes;
+                nnz += nb;
+                if (p->prm.mem_budget_bytes > 0 && p->info.g_bytes + h_bytes > p->prm.mem_budget_bytes)
+                    fail(RIMO_ERR_BUDGET, "holographic matrices need more than the " +
+                                              std::to_string(p->prm.mem_budget_bytes - p->info.g_bytes) +
+                                              " bytes the budget leaves beyond G");
+                if (keep_dense) {
+                    // the bin's coverage is dense: the temporary becomes the stored rows
+                    p->owned.push_back(dense.p);
+                    made.back() = dense.p;
+                    p->d_hval[b] = (float2*)dense.p;
+                    dense.p = nullptr;
+                    p->h_dense[b] = 1;
+                    continue;
+                }
+                made.pop_back();
+                p->d_hroff[b] = (int64_t*)keep(roff.size() * sizeof(int64_t));
+                RIMO_CUDA(cudaMemcpyAsync(p->d_hroff[b], roff.data(), roff.size() * sizeof(int64_t),
+                                          cudaMemcpyHostToDevice, s));
+                p->d_hval[b] = (float2*)keep((size_t)nb * sizeof(float2));
+                p->d_hidx[b] = (uint16_t*)keep((size_t)nb * sizeof(uint16_t));
+                hcompact_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2*)dense.p, nown, ne, p->d_hroff[b],
+                                                                 p->d_hval[b], p->d_hidx[b]);
+                RIMO_CUDA(cudaGetLastError());
+                RIMO_CUDA(cudaStreamSynchronize(s));  // the dense rows are freed next
+            } else {
+                p->d_hroff[b] = (int64_t*)keep(roff.size() * sizeof(int64_t));
+                RIMO_CUDA(cudaMemcpyAsync(p->d_hroff[b], roff.data(), roff.size() * sizeof(int64_t),
+                                          cudaMemcpyHostToDevice, s));
+                p->d_hval[b] = (float2*)keep(16);
+                p->d_hidx[b] = (uint16_t*)keep(16);
+            }
+        }
+        RIMO_CUDA(cudaMemcpyAsync(&diag, ddiag.p, sizeof(diag), cudaMemcpyDeviceToHost, s));
+        RIMO_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        cudaStreamSynchronize(s);
+        release_made();
+        throw;
     }
+    p->info.h_entries = total * ne;              // a dense stencil per covered cell
+    p->info.h_nonzero = nnz;                      // what the rows keep
+    p->info.h_nnz = 2 * (nnz - (int64_t)diag) + (int64_t)diag;
     p->h_ne = ne;
     p->info.h_bytes = h_bytes + (int64_t)patch_bytes;
     p->h_built = true;
@@ -717,8 +813,28 @@ rimo_status rimo_plan_get_holographic(rimo_plan_t p, int32_t bin, const int32_t*
         for (int w = 0; w < (cell >> 5); ++w) rank += __builtin_popcount(bm[w]);
         rank += __builtin_popcount(bm[cell >> 5] & ((1u << (cell & 31)) - 1u));
         const int64_t row = p->hoff_host[bin][(size_t)k] + rank;
+        if (p->h_dense[bin]) {
+            float2 h;
+            RIMO_CUDA(cudaMemcpyAsync(&h, p->d_hval[bin] + (size_t)row * p->h_ne + e, sizeof(h),
+                                      cudaMemcpyDeviceToHost, s));
+            RIMO_CUDA(cudaStreamSynchronize(s));
+            out[q] = rimo_cfloat{h.x, conj ? -h.y : h.y};
+            continue;
+        }
+        // the row keeps its non-zero entries, in entry order: find entry e among them
+        int64_t span[2];
+        RIMO_CUDA(cudaMemcpyAsync(span, p->d_hroff[bin] + row, sizeof(span), cudaMemcpyDeviceToHost, s));
+        RIMO_CUDA(cudaStreamSynchronize(s));
+        std::vector<uint16_t> ids((size_t)(span[1] - span[0]));
+        if (!ids.empty()) {
+            RIMO_CUDA(cudaMemcpyAsync(ids.data(), p->d_hidx[bin] + span[0], ids.size() * sizeof(uint16_t),
+                                      cudaMemcpyDeviceToHost, s));
+            RIMO_CUDA(cudaStreamSynchronize(s));
+        }
+        const auto it = std::lower_bound(ids.begin(), ids.end(), (uint16_t)e);
+        if (it == ids.end() || *it != (uint16_t)e) continue;  // a zero entry
         float2 h;
-        RIMO_CUDA(cudaMemcpyAsync(&h, p->d_hrows[bin] + (size_t)row * p->h_ne + e, sizeof(h), cudaMemcpyDeviceToHost, s));
+        RIMO_CUDA(cudaMemcpyAsync(&h, p->d_hval[bin] + span[0] + (it - ids.begin()), sizeof(h), cudaMemcpyDeviceToHost, s));
         RIMO_CUDA(cudaStreamSynchronize(s));
         out[q] = rimo_cfloat{h.x, conj ? -h.y : h.y};
     }

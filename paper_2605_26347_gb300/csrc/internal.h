@@ -156,7 +156,12 @@ struct rimo_plan {
     // its owner: the cell at the top-left corner of the pair's bounding box (see hmat.cu).
     bool h_built = false;
     int h_ne = 0;                         // entries per owner cell: (H+1)^2 + H^2
-    std::vector<float2*> d_hrows;         // per bin: [owner][h_ne]
+    // owner rows, per bin either dense (all h_ne entries per row) or keeping their non-zero
+    // entries only (Section 3.3: H is sparse), whichever is smaller: per bin
+    std::vector<float2*> d_hval;          //   the values, owner row after owner row
+    std::vector<uint16_t*> d_hidx;        //   compressed: their entry numbers e < h_ne
+    std::vector<int64_t*> d_hroff;        //   compressed: [owner + 1] first value of each row
+    std::vector<uint8_t> h_dense;         //   1: the bin's rows are dense
     std::vector<uint32_t*> d_htmax;       // per bin: [needed tile] max |h.x| + |h.y| (float bits)
     std::vector<uint32_t*> d_hbits;       // per bin: [needed tile][TS*TS/32] covered cells
     std::vector<int64_t*> d_hoff;         // per bin: [needed tile + 1] first owner of the tile
