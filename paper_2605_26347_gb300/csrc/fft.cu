@@ -116,6 +116,39 @@ __device__ __forceinline__ void dft16(float2* v) {
     for (int k = 0; k < 16; ++k) v[k] = t[k];
 }
 
+// dft16 of an input whose points 4 .. 11 are zero (the first stage of a forward pass, whose
+// row holds its samples in the centred half): the first layer of 4-point DFTs reduces to
+// sums and differences of x_n2 and x_n2+12 (written out, since the compiler may not drop an
+// addition of +0, which would turn -0 into +0)
+template <bool INV>
+__device__ __forceinline__ void dft16_hz(float2* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        const float2 a = v[n2], d = v[n2 + 12];
+        const float2 md = mul_mi<INV>(make_float2(-d.x, -d.y));
+        v[n2] = cadd(a, d);
+        v[n2 + 8] = csub(a, d);
+        v[n2 + 4] = cadd(a, md);
+        v[n2 + 12] = csub(a, md);
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) v[n2 + 4 * k1] = cmul(v[n2 + 4 * k1], w16<INV>(n2 * k1));
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a = v[0 + 4 * k1], b = v[1 + 4 * k1], c = v[2 + 4 * k1], d = v[3 + 4 * k1];
+        dft4<INV>(a, b, c, d);
+        t[k1 + 0] = a;
+        t[k1 + 4] = b;
+        t[k1 + 8] = c;
+        t[k1 + 12] = d;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2* v) {
     if constexpr (R == 2) dft2<INV>(v[0], v[1]);
@@ -131,7 +164,8 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 // a[j + r N/R] and writes a'[(j / NS) NS R + j % NS + r NS].  Its twiddles
 // W_{NS R}^{r (j mod NS)} come from the stage table tws[r NS + j mod NS], laid out so that
 // consecutive threads read consecutive entries.
-template <int N, int R, int NS, bool INV, bool FIRST, bool LAST>
+// HZ: a first stage whose inputs m = 4 .. 11 are zero (forward passes)
+template <int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool HZ = false>
 __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tws) {
     constexpr int T = N / 16;
     constexpr int Q = 16 / R;
@@ -148,7 +182,8 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
             const int jm = (t + q * T) & (NS - 1);
             if constexpr (R == 16) {
                 // W^r for r = 1 .. 15 from two table entries (W and W^4), at most three
-                // products deep: two loads instead of fifteen
+                // products deep: two loads instead of fifteen (fifteen loads from the table
+                // were slower: 49.0 against 48.4 ms per 4096^2/50M apply)
                 float2 w[16];
                 w[1] = __ldg(&tws[NS + jm]);
                 w[4] = __ldg(&tws[4 * NS + jm]);
@@ -169,7 +204,8 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
                 }
             }
         }
-        dft_r<R, INV>(&v[q * R]);
+        if constexpr (HZ && R == 16) dft16_hz<INV>(&v[q * R]);
+        else dft_r<R, INV>(&v[q * R]);
     }
     if (!LAST) {
 #pragma unroll
@@ -196,18 +232,18 @@ struct Plan16 {
 // tws: the stage twiddle tables of length N (see stage_twiddles on the host): the second
 // stage's W_{16 R}^{r j} at [0, 16 R), the third stage's W_{256 R}^{r j} at [256, 256 + 256 R),
 // a fourth stage's W_{4096 R}^{r j} at [4352, 4352 + 4096 R).
-template <int N, bool INV>
+template <int N, bool INV, bool HZ = false>
 __device__ __forceinline__ void fft_n(float2 (&v)[16], float2* sm, int t, const float2* __restrict__ tws) {
     constexpr int RL = Plan16<N>::R_LAST;
     if constexpr (Plan16<N>::STAGES == 2) {
-        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, 16, 1, INV, true, false, HZ>(v, sm, t, tws);
         fft_stage<N, RL, 16, INV, false, true>(v, sm, t, tws);
     } else if constexpr (Plan16<N>::STAGES == 3) {
-        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, 16, 1, INV, true, false, HZ>(v, sm, t, tws);
         fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tws);
         fft_stage<N, RL, 256, INV, false, true>(v, sm, t, tws + 256);
     } else {
-        fft_stage<N, 16, 1, INV, true, false>(v, sm, t, tws);
+        fft_stage<N, 16, 1, INV, true, false, HZ>(v, sm, t, tws);
         fft_stage<N, 16, 16, INV, false, false>(v, sm, t, tws);
         fft_stage<N, 16, 256, INV, false, false>(v, sm, t, tws + 256);
         fft_stage<N, RL, 4096, INV, false, true>(v, sm, t, tws + 256 + 4096);
@@ -464,7 +500,7 @@ __global__ void __launch_bounds__(RB * N / 8, (1024 / (RB * N / 8)) > 0 ? (1024 
             v[m] = cmul(__ldg(&xr[j]), z_factor(z, i, j, ic, jc));
         }
     }
-    fft_n<L, false>(v, sm, t, tws);
+    fft_n<L, false, true>(v, sm, t, tws);
 #pragma unroll
     for (int m = 0; m < 16; ++m) sm[pidx(t + T * m)] = v[out_slot<L>(m)];
     // rows k of At the forward column pass does not transform are not stored
@@ -510,7 +546,7 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
         }
     }
     __syncthreads();
-    fft_n<L, false>(v, sm, t, tws);
+    fft_n<L, false, true>(v, sm, t, tws);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int k = t + T * m;
