@@ -161,6 +161,11 @@ typedef struct rimo_plan_info {
                                /* some visibility's footprint covers together)       */
     int64_t h_nnz;             /* non-zeros of the full Hermitian H_p = G_p^H G_p,   */
                                /* summed over bins: both triangles and the diagonal  */
+    int64_t n_units;           /* grid-step work units over all bins (uv-tiles, or   */
+                               /* slices of the heaviest ones)                       */
+    int64_t box_cells;         /* sum over the units of their box (the cells their   */
+                               /* footprints reach; a split tile's slices: whole     */
+                               /* patches): X cells staged and patch cells stored    */
 } rimo_plan_info;
 
 typedef struct rimo_plan* rimo_plan_t;
@@ -534,6 +539,22 @@ rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_par
  */
 rimo_status rimo_autotune(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
                           void* stream, int32_t* tile_out, int32_t* order_out, double* ms_out);
+/*
+ * The same choice for a batch of workloads (the channels of a wideband batch, or a sample
+ * of them): for every candidate, one plan per workload (every ceil(M[i] / 2^22)-th row) is
+ * made and the plans are recorded as one batch (rimo_batch_create_form, RIMO_BATCH_AUTO),
+ * whose Phi^dagger Phi is timed; the pick is the fastest batch.  (Timing the channels one
+ * plan at a time does not rank the candidates as the batch does: there the per-bin launch
+ * costs, which a batch amortises, hide the grid step's share.)  uvw[i] (host, M[i] x 3) and
+ * base[i] describe workload i of n (base[i] with its own FoV and w-bins; one image size for
+ * all).  ms_out (host, 6 values, may be NULL): the batch's ms per apply for each candidate,
+ * or -1 when not timed.  Cache entries (key: the workloads' shape keys joined, suffix
+ * "_batch_tile_order") hold tile * 10 + order.  Allocates and frees 2 n images, n plans and
+ * one batch per candidate; synchronises `stream`.  Errors as rimo_autotune.
+ */
+rimo_status rimo_autotune_batch(const double* const* uvw, const int64_t* M, const rimo_plan_params* base, int32_t n,
+                                const char* cache_path, void* stream, int32_t* tile_out, int32_t* order_out,
+                                double* ms_out);
 
 /*
  * Data weighting injected into the measurement operator (Section 2, Eq. 3: a weighting

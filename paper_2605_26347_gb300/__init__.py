@@ -18,6 +18,7 @@ from ._lib import (MODE_AUTO, MODE_HOLOGRAPHIC, MODE_ONTHEFLY, MODE_STORED_G, MO
                    PlanInfo, PlanParams, RimoError)
 
 __all__ = ["Plan", "PlanParams", "PlanInfo", "RimoError", "default_params", "estimate", "Batch", "autotune_tile",
+           "autotune_batch",
            "MODE_AUTO", "MODE_STORED_G", "MODE_HOLOGRAPHIC", "MODE_SURROGATE", "MODE_ONTHEFLY"]
 
 
@@ -466,6 +467,25 @@ def autotune(uvw, params: PlanParams, cache_path: str | None = None, stream=None
     _lib.check(lib.rimo_autotune(u.ctypes.data, u.shape[0], C.byref(params), path, _stream_ptr(stream),
                                  C.byref(tile), C.byref(order), ms))
     return {"tile_size": tile.value, "uv_order": order.value, "ms": list(ms)}
+
+
+def autotune_batch(uvws, params, cache_path: str | None = None, stream=None) -> dict:
+    """rimo_autotune_batch: the uv-tile size and visibility order minimising the summed time
+    over several workloads (uvws[i] with params[i]), with the six summed timings."""
+    lib = _lib.load()
+    if len(uvws) != len(params) or not uvws:
+        raise ValueError("one parameter set per workload, at least one workload")
+    us = [_uvw_arg(u) for u in uvws]
+    n = len(us)
+    ptrs = (C.c_void_p * n)(*[u.ctypes.data for u in us])
+    ms_n = (C.c_int64 * n)(*[u.shape[0] for u in us])
+    prm = (PlanParams * n)(*params)
+    tile, order = C.c_int32(), C.c_int32()
+    ms = (C.c_double * 6)()
+    path = cache_path.encode() if cache_path else None
+    _lib.check(lib.rimo_autotune_batch(ptrs, ms_n, prm, n, path, _stream_ptr(stream), C.byref(tile), C.byref(order),
+                                       ms))
+    return {"tile_size": tile.value, "uv_order": order.value, "ms": list(ms), "workloads": n}
 
 
 def unpack_params(p: np.ndarray) -> dict:

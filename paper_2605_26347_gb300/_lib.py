@@ -73,6 +73,8 @@ class PlanInfo(C.Structure):
         ("h_entries", C.c_int64),
         ("h_nonzero", C.c_int64),
         ("h_nnz", C.c_int64),
+        ("n_units", C.c_int64),
+        ("box_cells", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -118,6 +120,7 @@ _PROTOS = {
     "rimo_batch_layout": (C.c_int, [_P, _P, _P, _P, _P]),
     "rimo_autotune_tile": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P]),
     "rimo_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(PlanParams), C.c_char_p, _P, _P, _P, _P]),
+    "rimo_autotune_batch": (C.c_int, [_P, _P, _P, C.c_int32, C.c_char_p, _P, _P, _P, _P]),
     "rimo_plan_set_surrogate": (C.c_int, [_P, _P]),
     "rimo_surrogate_fit": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P, _P]),
     "rimo_surrogate_get_w_scale": (C.c_int, [_P, C.POINTER(C.c_float)]),

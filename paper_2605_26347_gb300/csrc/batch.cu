@@ -427,6 +427,98 @@ int tune(const double* uvw, int64_t M, const rimo_plan_params* base, const std::
     return pick;
 }
 
+// The same for a batch: each candidate's plans (one per workload, every stride-th row of
+// each, at most 2^22 rows) recorded as one batch (the staged form where eligible) and its
+// Phi^dagger Phi timed; returns the index of the fastest, ms[c] the batch's ms per apply.
+int tune_batch(const double* const* uvw, const int64_t* M, const rimo_plan_params* base, int n,
+               const std::vector<std::pair<int, int>>& cands, void* stream, double* ms) {
+    const int64_t cap = 1 << 22;
+    std::vector<std::vector<double>> subs(n);
+    std::vector<const double*> src(n);
+    std::vector<int64_t> Ms(n);
+    for (int i = 0; i < n; ++i) {
+        if (base[i].nx != base[0].nx || base[i].ny != base[0].ny)
+            fail(RIMO_ERR_INVALID_ARG, "the workloads of a batch share one image size");
+        const int64_t stride = (M[i] + cap - 1) / cap;
+        src[i] = uvw[i];
+        Ms[i] = M[i];
+        if (stride > 1) {
+            Ms[i] = (M[i] + stride - 1) / stride;
+            subs[i].resize((size_t)Ms[i] * 3);
+            for (int64_t k = 0; k < Ms[i]; ++k)
+                for (int c = 0; c < 3; ++c) subs[i][(size_t)k * 3 + c] = uvw[i][(size_t)(k * stride) * 3 + c];
+            src[i] = subs[i].data();
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t img = (size_t)base[0].nx * base[0].ny;
+    float2 *x = nullptr, *o = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<rimo_plan_t> plans;
+    rimo_batch_t batch = nullptr;
+    auto release = [&]() {
+        rimo_batch_destroy(batch);
+        batch = nullptr;
+        for (rimo_plan_t p : plans) rimo_plan_destroy(p);
+        plans.clear();
+    };
+    double best = 1e300;
+    int pick = 0;
+    try {
+        RIMO_CUDA(cudaMalloc(&x, img * n * sizeof(float2)));
+        RIMO_CUDA(cudaMalloc(&o, img * n * sizeof(float2)));
+        RIMO_CUDA(cudaMemsetAsync(x, 0, img * n * sizeof(float2), s));
+        const float2 one = make_float2(1.f, 0.f);
+        for (int i = 0; i < n; ++i)  // a point at the centre of every image: every grid is non-trivial
+            RIMO_CUDA(cudaMemcpyAsync(x + i * img + (size_t)(base[0].ny / 2) * base[0].nx + base[0].nx / 2, &one,
+                                      sizeof(one), cudaMemcpyHostToDevice, s));
+        RIMO_CUDA(cudaEventCreate(&e0));
+        RIMO_CUDA(cudaEventCreate(&e1));
+        for (size_t c = 0; c < cands.size(); ++c) {
+            for (int i = 0; i < n; ++i) {
+                rimo_plan_params q = base[i];
+                q.tile_size = cands[c].first;
+                q.uv_order = cands[c].second;
+                rimo_plan_t p = nullptr;
+                if (rimo_plan_create(src[i], Ms[i], &q, stream, &p) != RIMO_OK)
+                    fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
+                plans.push_back(p);
+            }
+            if (rimo_batch_create_form(plans.data(), n, RIMO_BATCH_AUTO, &batch) != RIMO_OK)
+                fail(RIMO_ERR_INVALID_ARG, rimo_last_error());
+            auto apply = [&]() {
+                if (rimo_batch_apply_phi_adj_phi(batch, (const rimo_cfloat*)x, (rimo_cfloat*)o, 0, stream) != RIMO_OK)
+                    fail(RIMO_ERR_CUDA, rimo_last_error());
+            };
+            apply();  // records the graph
+            RIMO_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) apply();
+            RIMO_CUDA(cudaEventRecord(e1, s));
+            RIMO_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            RIMO_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            release();
+            ms[c] = t / 3.0;
+            if (ms[c] < best) {
+                best = ms[c];
+                pick = (int)c;
+            }
+        }
+    } catch (...) {
+        release();
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(x);
+        cudaFree(o);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(o);
+    return pick;
+}
+
 // cache key of a workload's shape (image, FoV, log2 M, P, J, largest tile side), from a
 // host-only estimate on the same subsample the tuner times
 std::string shape_key(const double* uvw, int64_t M, const rimo_plan_params* base, const char* suffix) {
@@ -442,6 +534,44 @@ std::string shape_key(const double* uvw, int64_t M, const rimo_plan_params* base
 }  // namespace
 
 extern "C" {
+
+rimo_status rimo_autotune_batch(const double* const* uvw, const int64_t* M, const rimo_plan_params* base, int32_t n,
+                                const char* cache_path, void* stream, int32_t* tile_out, int32_t* order_out,
+                                double* ms_out) {
+    RIMO_API_BEGIN
+    if (!uvw || !M || !base || n <= 0 || !tile_out || !order_out) fail(RIMO_ERR_INVALID_ARG, "null argument or n <= 0");
+    for (int i = 0; i < n; ++i)
+        if (!uvw[i] || M[i] <= 0) fail(RIMO_ERR_INVALID_ARG, "null or empty workload");
+    if (ms_out)
+        for (int i = 0; i < 6; ++i) ms_out[i] = -1.0;
+    std::string key;
+    for (int i = 0; i < n; ++i) key += (i ? "+" : "") + shape_key(uvw[i], M[i], &base[i], "");
+    key += "_batch_tile_order";
+    std::map<std::string, int> cache;
+    if (cache_path && *cache_path) {
+        cache = read_cache(cache_path);
+        auto it = cache.find(key);
+        if (it != cache.end() && (it->second / 10 == 32 || it->second / 10 == 64) && it->second % 10 <= 2) {
+            *tile_out = it->second / 10;
+            *order_out = it->second % 10;
+            return RIMO_OK;
+        }
+    }
+    std::vector<std::pair<int, int>> cands;
+    for (int t : {32, 64})
+        for (int o = 0; o < 3; ++o) cands.push_back({t, o});
+    double ms[6];
+    const int pick = tune_batch(uvw, M, base, n, cands, stream, ms);
+    if (ms_out)
+        for (int i = 0; i < 6; ++i) ms_out[i] = ms[i];
+    *tile_out = cands[pick].first;
+    *order_out = cands[pick].second;
+    if (cache_path && *cache_path) {
+        cache[key] = *tile_out * 10 + *order_out;
+        write_cache(cache_path, cache);
+    }
+    RIMO_API_END
+}
 
 rimo_status rimo_autotune_tile(const double* uvw, int64_t M, const rimo_plan_params* base, const char* cache_path,
                                void* stream, int32_t* tile_out, double* ms_out) {

@@ -561,6 +561,8 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
 // patch reaches are never written and read as zero by the inverse transform.
 struct FoldArgs {
     const float2* patch;   // [slot][PW * PW]
+    const int2* slotbox;   // [tu * ntv + tv] -> (slot or -1, the slot's box: cells outside it
+                           //   are zero and not stored), or null: `slot` with whole patches
     const int* slot;       // [tu * ntv + tv] -> slot or -1 (this bin)
     const int* tiles;      // needed tiles of this bin, tu * ntv + tv
     float2* Xh;            // [gx][gy]
@@ -575,17 +577,46 @@ __global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ FoldA
     const int tu = tile / F.ntv, tv = tile - tu * F.ntv;
     const int tu1 = tu == 0 ? F.ntu - 1 : tu - 1, tv1 = tv == 0 ? F.ntv - 1 : tv - 1;
     const size_t np = (size_t)F.PW * F.PW;
-    const int s00 = F.slot[tu * F.ntv + tv], s10 = F.slot[tu1 * F.ntv + tv];
-    const int s01 = F.slot[tu * F.ntv + tv1], s11 = F.slot[tu1 * F.ntv + tv1];
+    const uint32_t whole = box_pack(0, F.PW, 0, F.PW);
+    // slot and box of tile t (an empty box for a tile without a patch)
+    auto get = [&](int t, int& sl) {
+        if (F.slotbox) {
+            const int2 q = F.slotbox[t];
+            sl = q.x;
+            return sl < 0 ? 0u : (uint32_t)q.y;
+        }
+        sl = F.slot[t];
+        return sl < 0 ? 0u : whole;
+    };
+    int s00, s10, s01, s11;
+    const uint32_t x00 = get(tu * F.ntv + tv, s00), x10 = get(tu1 * F.ntv + tv, s10);
+    const uint32_t x01 = get(tu * F.ntv + tv1, s01), x11 = get(tu1 * F.ntv + tv1, s11);
+    // a box in the tile's cells (a, b): patch cells (a + oa, b + ob) with (oa, ob) the tile's
+    // offset in that patch; [lo, lo + n) per axis, compared unsigned (empty: n = 0)
+    struct Rng {
+        int a, na, b, nb;
+    };
+    auto rng = [&](uint32_t x, int oa, int ob) {
+        Rng r;
+        r.a = (int)(x & 255u) - oa;
+        r.na = max(0, (int)((x >> 8) & 255u) - oa - r.a);
+        r.b = (int)((x >> 16) & 255u) - ob;
+        r.nb = max(0, (int)(x >> 24) - ob - r.b);
+        return r;
+    };
+    auto in = [](const Rng& r, int a, int b) {
+        return (unsigned)(a - r.a) < (unsigned)r.na && (unsigned)(b - r.b) < (unsigned)r.nb;
+    };
+    const Rng r00 = rng(x00, 0, 0), r10 = rng(x10, F.TS, 0), r01 = rng(x01, 0, F.TS), r11 = rng(x11, F.TS, F.TS);
     const float2* __restrict__ patch = F.patch;
     float2* __restrict__ Xh = F.Xh;
     for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
         const int a = e / F.TS, b = e - a * F.TS;
         float2 acc = make_float2(0.f, 0.f);
-        if (s00 >= 0) acc = patch[s00 * np + a * F.PW + b];
-        if (a < F.H && s10 >= 0) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
-        if (b < F.H && s01 >= 0) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
-        if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
+        if (in(r00, a, b)) acc = patch[s00 * np + a * F.PW + b];
+        if (in(r10, a, b)) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
+        if (in(r01, a, b)) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
+        if (in(r11, a, b)) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
         Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
     }
 }
@@ -825,11 +856,14 @@ static ColsJob cols_job(const rimo_plan* p, int bin, const float2* in, float2* o
 }
 // grid-step patches (one per active tile, merged) or holographic-apply patches (one per
 // needed tile): both cover [tile origin, + PW) on each axis
-static FoldArgs fold_args(const rimo_plan* p, int bin, const float2* patch, const int* slot, float2* Xh) {
+// the grid step's patches (slots and boxes from the plan) or, with `hslot`, the holographic
+// apply's whole patches
+static FoldArgs fold_args(const rimo_plan* p, int bin, const float2* patch, const int* hslot, float2* Xh) {
     const int ntu = p->gx / p->TS, ntv = p->gy / p->TS;
     FoldArgs F;
     F.patch = patch;
-    F.slot = slot + (size_t)bin * ntu * ntv;
+    F.slotbox = hslot ? nullptr : p->d_slot + (size_t)bin * ntu * ntv;
+    F.slot = hslot ? hslot + (size_t)bin * ntu * ntv : nullptr;
     F.tiles = p->d_need_list + p->bins[bin].n0;
     F.Xh = Xh;
     F.ntu = ntu;
@@ -932,7 +966,7 @@ static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, c
 template <int N>
 static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStream_t s) {
     const auto& br = p->bins[bin];
-    run_fold<false>(fold_args(p, bin, holo ? p->d_hpatch : p->d_patch, holo ? p->d_hslot : p->d_slot, p->d_X),
+    run_fold<false>(fold_args(p, bin, holo ? p->d_hpatch : p->d_patch, holo ? p->d_hslot : nullptr, p->d_X),
                     no_table<FoldArgs>(), br.n1 - br.n0, s);
     const RowSel sel = inv_sel(p, bin);
     run_inv_cols<N, false>(cols_job(p, bin, p->d_X, B, sel), no_table<ColsJob>(),
@@ -1010,7 +1044,7 @@ WideFft* wide_fft_create(const std::vector<WideJob>& jobs, const std::vector<con
             frf.push_back(frf.back() + p->ny / rb);
             cf.push_back(cols_job(p, j.bin, j.AB, j.X, fs));
             fcf.push_back(fcf.back() + sel_blocks(p, j.bin, fs, rb));
-            fo.push_back(fold_args(p, j.bin, j.patch, p->d_slot, j.X));
+            fo.push_back(fold_args(p, j.bin, j.patch, nullptr, j.X));
             ffo.push_back(ffo.back() + (p->bins[j.bin].n1 - p->bins[j.bin].n0));
             ci.push_back(cols_job(p, j.bin, j.X, j.AB, is));
             fci.push_back(fci.back() + sel_blocks(p, j.bin, is, rb));

@@ -350,17 +350,22 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
                 int sq;
                 const GtgJob* Jq = unit_job<TABLE>(A, iq, sq);
                 const TileDesc tq = Jq->units[sq];
-                const int PW = PWC > 0 ? PWC : (TABLE ? Jq->PW : A.PW), npatch = PW * PW;
+                const int PW = PWC > 0 ? PWC : (TABLE ? Jq->PW : A.PW);
                 float2* dst = Xbuf0 + (size_t)j * npmax;
                 const int u0 = tq.tu * A.TS, v0 = tq.tv * A.TS;
                 const int n1 = (v0 + PW <= A.gy) ? PW : A.gy - v0;  // cells before the wrap
-                mbar_arrive_expect_tx(&xfull[j], (uint32_t)(npatch * sizeof(float2)));
-                for (int a = 0; a < PW; ++a) {
+                // the rows of the unit's box, its columns widened to whole 16-byte pairs
+                // (PW, TS, gy and n1 are even)
+                const int a0 = (int)(tq.box & 255u), a1 = (int)((tq.box >> 8) & 255u);
+                const int c0 = (int)((tq.box >> 16) & 254u), c1 = min(PW, (int)(((tq.box >> 24) + 1u) & 254u));
+                const int w1 = max(0, min(c1, n1) - c0), cs = max(c0, n1), w2 = max(0, c1 - cs);
+                mbar_arrive_expect_tx(&xfull[j], (uint32_t)((a1 - a0) * (w1 + w2) * (int)sizeof(float2)));
+                for (int a = a0; a < a1; ++a) {
                     int gu = u0 + a;
                     if (gu >= A.gx) gu -= A.gx;
                     const float2* row = Jq->X + (size_t)gu * A.gy;
-                    bulk_g2s(dst + a * PW, row + v0, (uint32_t)(n1 * sizeof(float2)), &xfull[j]);
-                    if (n1 < PW) bulk_g2s(dst + a * PW + n1, row, (uint32_t)((PW - n1) * sizeof(float2)), &xfull[j]);
+                    if (w1 > 0) bulk_g2s(dst + a * PW + c0, row + v0 + c0, (uint32_t)(w1 * sizeof(float2)), &xfull[j]);
+                    if (w2 > 0) bulk_g2s(dst + a * PW + cs, row + (cs - n1), (uint32_t)(w2 * sizeof(float2)), &xfull[j]);
                 }
                 ++xq;
             }
@@ -408,16 +413,19 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
         const int nchunks = (int)((td.ve - td.vb + GTG_CV - 1) / GTG_CV);
         const int PW = PWC > 0 ? PWC : (TABLE ? J->PW : A.PW), npatch = PW * PW;
         const int u0 = td.tu * A.TS, v0 = td.tv * A.TS;
+        // the unit's box: the only cells its footprints read and write
+        const int ba0 = (int)(td.box & 255u), ba1 = (int)((td.box >> 8) & 255u);
+        const int bb0 = (int)((td.box >> 16) & 255u), bb1 = (int)(td.box >> 24);
         float xm = 0.f;
         float2* Xs = Xbuf0 + (pre ? (size_t)(r % NX) * npmax : 0);
         if (pre && !s_abort && !mbar_wait_or_abort(&xfull[r % NX], (r / NX) & 1, &s_abort)) {
             s_abort = 1;
             atomicExch(J->status, 1);
         }
-        for (int a = warp; a < PW; a += GTG_CONSUMERS) {
+        for (int a = ba0 + warp; a < ba1; a += GTG_CONSUMERS) {
             int gu = u0 + a;
             if (gu >= A.gx) gu -= A.gx;
-            for (int b = lane; b < PW; b += 32) {
+            for (int b = bb0 + lane; b < bb1; b += 32) {
                 if (GATHER) {
                     float2 x;
                     if (pre) {
@@ -485,11 +493,17 @@ __global__ void __launch_bounds__(GTG_THREADS, 1) gtg_kernel(const __grid_consta
         }
         consumers_sync();
         if (SCATTER && !s_abort) {
+            // the box of the patch (the fold and the merge read no cell outside it)
             float2* dst = J->patch + (size_t)slot * npatch;
             const float inv_lo = inv_s1 * (1.f / 65536.f);
-            for (int e = tid; e < npatch; e += GTG_CONSUMERS * 32) {
-                const int2 h = reinterpret_cast<const int2*>(Ahi)[e], l = reinterpret_cast<const int2*>(Alo)[e];
-                dst[e] = make_float2(fmaf((float)l.x, inv_lo, (float)h.x * inv_s1),
+            const int bw = bb1 - bb0, nb = (ba1 - ba0) * bw;
+            // e / bw = umulhi(e, ceil(2^32 / bw)) while e bw < 2^32 (e < PW^2, bw <= PW)
+            const uint32_t mg = 0xffffffffu / (uint32_t)max(bw, 2) + 1u;
+            for (int e = tid; e < nb; e += GTG_CONSUMERS * 32) {
+                const int da = bw > 1 ? (int)__umulhi((uint32_t)e, mg) : e;
+                const int c = (ba0 + da) * PW + bb0 + (e - da * bw);
+                const int2 h = reinterpret_cast<const int2*>(Ahi)[c], l = reinterpret_cast<const int2*>(Alo)[c];
+                dst[c] = make_float2(fmaf((float)l.x, inv_lo, (float)h.x * inv_s1),
                                      fmaf((float)l.y, inv_lo, (float)h.y * inv_s1));
             }
         }

@@ -60,7 +60,14 @@ struct TileDesc {
     int32_t tu, tv;
     int64_t vb, ve;
     int64_t cb;   // index of the unit's first chunk descriptor
+    // the unit's box within its patch: the cells [a0, a1) x [b0, b1) its footprints reach
+    // (a0 | a1 << 8 | b0 << 16 | b1 << 24); the whole patch for the units of a split tile
+    uint32_t box;
+    uint32_t pad_;
 };
+__host__ __device__ inline uint32_t box_pack(int a0, int a1, int b0, int b1) {
+    return (uint32_t)a0 | ((uint32_t)a1 << 8) | ((uint32_t)b0 << 16) | ((uint32_t)b1 << 24);
+}
 
 // One chunk of at most GTG_CHUNK consecutive visibilities of a unit: their taps are the byte
 // range [8 off, 8 off + bytes) of Fourier block `block`.
@@ -127,7 +134,8 @@ struct rimo_plan {
     float* d_phiv = nullptr;
     float2* d_X = nullptr;     // forward grid   (gx rows u, gy cols v)
     float2* d_patch = nullptr; // gridded accumulator patch of every active tile of one bin
-    int32_t* d_slot = nullptr; // [bin][tu][tv] -> index of the tile's patch in d_patch, or -1
+    int2* d_slot = nullptr;    // [bin][tu][tv] -> (index of the tile's patch in d_patch, or -1;
+                               //   the box of that patch, TileDesc::box)
     uint8_t* d_need = nullptr; // [bin][tu][tv] != 0: some active patch of the bin reads the tile
     int32_t* d_need_list = nullptr;  // per bin: the needed tiles as tu * ntv + tv
     int32_t* d_counter = nullptr;  // per-bin dynamic tile schedulers (reset at each apply)

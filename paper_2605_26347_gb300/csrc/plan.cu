@@ -477,7 +477,22 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
             const int64_t k = (n + cap - 1) / cap;
             for (int64_t q = 0; q < k; ++q) {
                 const int64_t a = x.vb + n * q / k, e = x.vb + n * (q + 1) / k;
-                p->tiles_host.push_back(TileDesc{x.tu, x.tv, a, e, 0});
+                TileDesc u{x.tu, x.tv, a, e, 0, 0u, 0u};
+                if (k > 1) {
+                    u.box = box_pack(0, p->PW, 0, p->PW);  // the merge adds the slices' whole patches
+                } else {
+                    int a0 = p->PW, a1 = 0, b0 = p->PW, b1 = 0;
+                    for (int64_t i = a; i < e; ++i) {
+                        const uint32_t pos = meta[i].pos;
+                        const int du = (int)(pos & 255u), dv = (int)((pos >> 8) & 255u), S = (int)((pos >> 16) & 255u);
+                        a0 = std::min(a0, du);
+                        a1 = std::max(a1, du + S);
+                        b0 = std::min(b0, dv);
+                        b1 = std::max(b1, dv + S);
+                    }
+                    u.box = box_pack(a0, a1, b0, b1);
+                }
+                p->tiles_host.push_back(u);
             }
             slot[(size_t)b * ntile + (size_t)x.tu * ntv + x.tv] = first;
             if (k > 1) p->merge_host.push_back(make_int2(first, (int)k));
@@ -559,7 +574,17 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     // every cell finite from the start: the gridding step may stage cells that no footprint
     // of the current bin reaches
     RIMO_CUDA(cudaMemsetAsync(p->d_X, 0, grid_elems * sizeof(float2), s));
-    p->d_slot = upload(p, slot, s);
+    {
+        // the fold reads a tile's slot and the box of that slot's patch in one load
+        std::vector<int2> sb(slot.size());
+        for (int b = 0; b < P; ++b)
+            for (int64_t t = 0; t < ntile; ++t) {
+                const int32_t sl = slot[(size_t)b * ntile + t];
+                sb[(size_t)b * ntile + t] =
+                    make_int2(sl, sl < 0 ? 0 : (int)p->tiles_host[(size_t)p->bins[b].t0 + sl].box);
+            }
+        p->d_slot = upload(p, sb, s);
+    }
     {
         // tiles of X read by the patch of some active tile: the tile itself and its
         // neighbours after it along u, v and both (the patch reaches H cells past the tile)
@@ -619,6 +644,10 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
                                       (size_t)p->max_tiles_bin * p->PW * p->PW) * 8 + p->sur_taps_bytes;
     p->info.n_blocks = (int32_t)p->block_bytes.size();
     p->info.n_tiles = n_active;
+    p->info.n_units = (int64_t)p->tiles_host.size();
+    p->info.box_cells = 0;
+    for (const TileDesc& u : p->tiles_host)
+        p->info.box_cells += (int64_t)(((u.box >> 8) & 255u) - (u.box & 255u)) * (int64_t)((u.box >> 24) - ((u.box >> 16) & 255u));
 
     // ---- stage 3: precompute G on the device (the surrogate generates it at apply time)
     if (!generated) {

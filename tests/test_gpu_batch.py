@@ -172,3 +172,23 @@ def test_visibility_orders_match_the_oracle(order):
     ref = op.phi_adj_phi(w.sky.astype(np.complex128))
     assert rel(to_host(plan.phi_adj_phi(to_dev(w.sky))), ref) < TOL
     plan.close()
+
+
+def test_batch_autotuner_times_the_batch_and_caches(tmp_path):
+    import paper_2605_26347_gb300 as pkg
+    fov = math.radians(2.0)
+    uvws = [synth.make_uvw(20000, 600, 1.0e9, 81), synth.make_uvw(30000, 600, 1.5e9, 82)]
+    params = [pkg.default_params(256, 256, fov, fov, n_wbins=2), pkg.default_params(256, 256, fov, fov, n_wbins=3)]
+    cache = tmp_path / "tune.json"
+    r = pkg.autotune_batch(uvws, params, str(cache))
+    assert r["workloads"] == 2 and len(r["ms"]) == 6 and min(r["ms"]) > 0
+    best = int(np.argmin(r["ms"]))
+    assert (r["tile_size"], r["uv_order"]) == ((32, 64)[best // 3], best % 3)
+    key = [k for k in json.loads(cache.read_text()) if k.endswith("_batch_tile_order")]
+    assert len(key) == 1 and "+" in key[0]
+    r2 = pkg.autotune_batch(uvws, params, str(cache))        # cache hit: nothing timed
+    assert (r2["tile_size"], r2["uv_order"]) == (r["tile_size"], r["uv_order"]) and r2["ms"] == [-1.0] * 6
+    with pytest.raises(ValueError):
+        pkg.autotune_batch(uvws, params[:1])
+    with pytest.raises(pkg.RimoError):   # the workloads of a batch share one image size
+        pkg.autotune_batch(uvws, [params[0], pkg.default_params(128, 128, fov, fov, n_wbins=2)])
