@@ -610,6 +610,21 @@ __global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ FoldA
     const Rng r00 = rng(x00, 0, 0), r10 = rng(x10, F.TS, 0), r01 = rng(x01, 0, F.TS), r11 = rng(x11, F.TS, F.TS);
     const float2* __restrict__ patch = F.patch;
     float2* __restrict__ Xh = F.Xh;
+    // every box covers all the cells its patch gives this tile (dense units): no per-cell test
+    auto covers = [](const Rng& r, int na, int nb) { return r.a <= 0 && r.a + r.na >= na && r.b <= 0 && r.b + r.nb >= nb; };
+    if ((s00 < 0 || covers(r00, F.TS, F.TS)) && (s10 < 0 || covers(r10, F.H, F.TS)) &&
+        (s01 < 0 || covers(r01, F.TS, F.H)) && (s11 < 0 || covers(r11, F.H, F.H))) {
+        for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
+            const int a = e / F.TS, b = e - a * F.TS;
+            float2 acc = make_float2(0.f, 0.f);
+            if (s00 >= 0) acc = patch[s00 * np + a * F.PW + b];
+            if (a < F.H && s10 >= 0) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
+            if (b < F.H && s01 >= 0) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
+            if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
+            Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
         const int a = e / F.TS, b = e - a * F.TS;
         float2 acc = make_float2(0.f, 0.f);

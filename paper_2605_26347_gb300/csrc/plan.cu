@@ -586,16 +586,21 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         p->d_slot = upload(p, sb, s);
     }
     {
-        // tiles of X read by the patch of some active tile: the tile itself and its
-        // neighbours after it along u, v and both (the patch reaches H cells past the tile)
+        // tiles of X read by the patch of some active tile: the tile itself and those of its
+        // neighbours after it along u, v and both that the box of its patch reaches (a box
+        // starts inside its own tile and ends at most H cells past it)
         std::vector<uint8_t> need((size_t)P * ntile, 0);
         for (int b = 0; b < P; ++b)
             for (int tu = 0; tu < ntu; ++tu)
                 for (int tv = 0; tv < ntv; ++tv) {
-                    if (slot[(size_t)b * ntile + (size_t)tu * ntv + tv] < 0) continue;
+                    const int32_t sl = slot[(size_t)b * ntile + (size_t)tu * ntv + tv];
+                    if (sl < 0) continue;
+                    const uint32_t box = p->tiles_host[(size_t)p->bins[b].t0 + sl].box;
+                    const bool down = (int)((box >> 8) & 255u) > TS, right = (int)(box >> 24) > TS;
                     for (int du = 0; du < 2; ++du)
                         for (int dv = 0; dv < 2; ++dv)
-                            need[(size_t)b * ntile + (size_t)((tu + du) % ntu) * ntv + (tv + dv) % ntv] = 1;
+                            if ((du == 0 || down) && (dv == 0 || right))
+                                need[(size_t)b * ntile + (size_t)((tu + du) % ntu) * ntv + (tv + dv) % ntv] = 1;
                 }
         p->d_need = upload(p, need, s);
         std::vector<int32_t> nl;
