@@ -12,7 +12,11 @@
 //                accumulated into the output image.
 //
 // Each pass is one 2N-point Stockham radix-16 FFT per row held in registers (16 points per
-// thread, 2N/16 threads per row), exchanging through shared memory between stages.  The
+// thread, 2N/16 threads per row), exchanging through shared memory between stages; at
+// 2N = 8192 the two column passes hold 32 points per thread instead (256 threads per row,
+// radix 32 x 16 x 16: two exchanges and barriers instead of three; measured per 4096^2/50M
+// apply, forward cols 4.28 -> 3.81 ms and inverse cols + fold 7.56 -> 6.90 ms, while the row
+// passes, which also evaluate Z_p per point, were slower so: 5.32 -> 5.55 and 4.30 -> 4.61 ms).  The
 // zero padding and the crop are exploited where they cost nothing: forward passes never
 // load the zero half of their input (those points enter the first butterflies as
 // constants), inverse passes store only the kept half of their output, and the
@@ -221,6 +225,114 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], float2* sm, int t, co
 
 // Radix plan of an L-point transform: 16, then 16s, then the remainder; L <= 256: two
 // stages (16, L/16), L <= 4096: three (16, 16, L/256), L = 8192: four (16, 16, 16, 2).
+// ----------------------------------------------------------------------------- 32 points per thread
+// The 8192-point transform with 256 threads of 32 points (radix 32, 16, 16): two
+// shared-memory exchanges instead of three.  Exchange buffer index i + i / 32 (the stride-32
+// writes of the first stage spread over the banks).
+__device__ __forceinline__ int pidx32(int i) { return i + (i >> 5); }
+
+#define C32_1 0.98078528040323044913f
+#define S32_1 0.19509032201612826785f
+#define C32_3 0.83146961230254523708f
+#define S32_3 0.55557023301960222474f
+
+// W_32^k, k in [0, 16): forward e^{-2 pi i k / 32}, inverse its conjugate
+template <bool INV>
+__device__ __forceinline__ float2 w32(int k) {
+    const float c[16] = {1.f, C32_1, C16, C32_3, RS2, S32_3, S16, S32_1, 0.f, -S32_1, -S16, -S32_3, -RS2, -C32_3, -C16, -C32_1};
+    const float s[16] = {0.f, S32_1, S16, S32_3, RS2, C32_3, C16, C32_1, 1.f, C32_1, C16, C32_3, RS2, S32_3, S16, S32_1};
+    return make_float2(c[k], INV ? s[k] : -s[k]);
+}
+
+// 32-point DFT in place: v[r] in natural order in and out (even / odd halves by dft16, then
+// one radix-2 layer with W_32^k).  HZ: inputs 8 .. 23 are zero.
+template <bool INV, bool HZ>
+__device__ __forceinline__ void dft32(float2* v) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        e[n] = v[2 * n];
+        o[n] = v[2 * n + 1];
+    }
+    if constexpr (HZ) {
+        // e[n] = x[2n], o[n] = x[2n + 1]: zero for 2n (+1) in [8, 24), i.e. n in [4, 12)
+        dft16_hz<INV>(e);
+        dft16_hz<INV>(o);
+    } else {
+        dft16<INV>(e);
+        dft16<INV>(o);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float2 t = k == 0 ? o[0] : cmul(o[k], w32<INV>(k));
+        v[k] = cadd(e[k], t);
+        v[k + 16] = csub(e[k], t);
+    }
+}
+
+// tws32 layout as in DevTables.  In: v[m] = element t + 256 m.  Out: v[s] is element
+// out_k32(t, s).  All 256 threads of the row must call it.
+template <bool INV, bool HZ>
+__device__ __forceinline__ void fft8192_32(float2 (&v)[32], float2* sm, int t, const float2* __restrict__ tw) {
+    dft32<INV, HZ>(v);  // stage 1: butterfly j = t, outputs at 32 t + r
+#pragma unroll
+    for (int r = 0; r < 32; ++r) sm[pidx32(32 * t + r)] = v[r];
+    __syncthreads();
+    // stage 2: NS = 32, R = 16, butterflies j = t + 256 q, reads j + 512 r
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[16 * q + r] = sm[pidx32(t + 256 * q + 512 * r)];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = t + 256 * q, jm = j & 31;
+        float2 w[16];
+        w[1] = __ldg(&tw[32 + jm]);
+        w[4] = __ldg(&tw[4 * 32 + jm]);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        w[8] = cmul(w[4], w[4]);
+#pragma unroll
+        for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[16 * q + r] = INV ? cmulc(v[16 * q + r], w[r]) : cmul(v[16 * q + r], w[r]);
+        dft16<INV>(&v[16 * q]);
+        const int base = (j >> 5) * 512 + jm;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm[pidx32(base + 32 * r)] = v[16 * q + r];
+    }
+    __syncthreads();
+    // stage 3: NS = 512, R = 16, butterflies j = t + 256 q (< 512), reads j + 512 r
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[16 * q + r] = sm[pidx32(t + 256 * q + 512 * r)];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int jm = t + 256 * q;
+        const float2* __restrict__ tw3 = tw + 512;
+        float2 w[16];
+        w[1] = __ldg(&tw3[512 + jm]);
+        w[4] = __ldg(&tw3[4 * 512 + jm]);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        w[8] = cmul(w[4], w[4]);
+#pragma unroll
+        for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[16 * q + r] = INV ? cmulc(v[16 * q + r], w[r]) : cmul(v[16 * q + r], w[r]);
+        dft16<INV>(&v[16 * q]);
+    }
+}
+// output index of v[s] after fft8192_32 in thread t: j = t + 256 (s / 16), k = j + 512 (s mod 16)
+__device__ __forceinline__ int out_k32(int t, int s) { return t + 256 * (s >> 4) + 512 * (s & 15); }
+
 template <int N>
 struct Plan16 {
     static constexpr int STAGES = N <= 256 ? 2 : (N <= 4096 ? 3 : 4);
@@ -552,6 +664,76 @@ __global__ void __launch_bounds__(RG * N / 8, (1024 / (RG * N / 8)) > 0 ? (1024 
         const int k = t + T * m;
         if (s_need[g * ntv + (k >> shift)]) out[k] = v[out_slot<L>(m)];
     }
+}
+
+// The same pass for N = 4096 with 256 threads of 32 points per row (one row per block).
+template <bool TABLE>
+__global__ void __launch_bounds__(256, 2)
+    fwd_cols32_kernel(const __grid_constant__ ColsJob one, const JobTable<ColsJob> tab, int shift,
+                      const float2* __restrict__ tw) {
+    constexpr int N = 4096, L = 8192;
+    extern __shared__ float2 smem[];
+    int bk;
+    const ColsJob& J = block_job<TABLE>(one, tab, bk);
+    const uint8_t* __restrict__ need = J.need;
+    const int ntv = L >> shift;
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + L + L / 32);
+    const int t = threadIdx.x;
+    const int r0 = sel_row0(J.sel, bk, 1);
+    const size_t u = (size_t)r0;
+    const float2* __restrict__ in = J.in + u * N;
+    float2* __restrict__ out = J.out + u * L;
+    for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = need[(u >> shift) * ntv + e];
+    float2 v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        if (m >= 8 && m < 24) {
+            v[m] = make_float2(0.f, 0.f);
+        } else {
+            const int p = t + 256 * m;
+            const int jc = m < 8 ? p : p - L;
+            v[m] = __ldg(&in[jc + N / 2]);
+        }
+    }
+    __syncthreads();
+    fft8192_32<false, true>(v, smem, t, tw);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int k = out_k32(t, q);
+        if (s_need[k >> shift]) out[k] = v[q];
+    }
+}
+
+// Inverse cols, N = 4096, 256 threads of 32 points per row, 4-CTA clusters for the store.
+template <bool TABLE>
+__global__ void __launch_bounds__(256, 2)
+    inv_cols32_kernel(const __grid_constant__ ColsJob one, const JobTable<ColsJob> tab, int gx, int shift,
+                      const float2* __restrict__ tw) {
+    constexpr int N = 4096, L = 8192, SR = L + L / 16;
+    extern __shared__ float2 smem[];
+    int bk;
+    const ColsJob& J = block_job<TABLE>(one, tab, bk);
+    const uint8_t* __restrict__ need = J.need;
+    const int ntv = L >> shift;
+    uint8_t* s_need = reinterpret_cast<uint8_t*>(smem + SR);
+    const int t = threadIdx.x;
+    const int r0 = sel_row0(J.sel, bk, 1);
+    const int u = r0;
+    for (int e = threadIdx.x; e < ntv; e += blockDim.x) s_need[e] = need[(size_t)(u >> shift) * ntv + e];
+    __syncthreads();
+    const float2* __restrict__ in = J.in + (size_t)u * L;
+    float2 v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const int p = t + 256 * m;
+        v[m] = s_need[p >> shift] ? __ldg(&in[p]) : make_float2(0.f, 0.f);
+    }
+    fft8192_32<true, false>(v, smem, t, tw);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) smem[pidx(out_k32(t, q))] = v[q];
+    transposed_store<1, 4, SR, N, 256>(
+        smem, [](int kk) { return kk < N / 2 ? kk : kk + N; },
+        [](int kk) { return kk < N / 2 ? kk + N / 2 : kk - N / 2; }, [](int) { return true; }, J.out, (size_t)gx, r0);
 }
 
 // ----------------------------------------------------------------------------- patch fold
@@ -909,9 +1091,19 @@ static void run_fwd_rows(const RowsJob& one, const JobTable<RowsJob>& tab, int g
     }
 }
 
+// The column passes at 2N = 8192 use the 32-points-per-thread transform (tw32: the plan's
+// tws32), the others the 16-point one.
 template <int N, bool TABLE>
 static void run_fwd_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int grid, int TS, const float2* tws,
-                         cudaStream_t s) {
+                         cudaStream_t s, const float2* tw32) {
+    if constexpr (N == 4096) {
+        if (!tw32) fail(RIMO_ERR_STATE, "8192-point column transforms without their twiddle table");
+        const size_t sm = (size_t)(8192 + 8192 / 32) * sizeof(float2) + 8192 / 32 + 16;
+        if (grid == 0) return;
+        set_smem(fwd_cols32_kernel<TABLE>, sm);
+        fwd_cols32_kernel<TABLE><<<grid, 256, sm, s>>>(one, tab, tile_shift(TS), tw32);
+        return;
+    }
     constexpr int RG = rows_per_block<N>();
     const int ntv = (2 * N) / TS;
     const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
@@ -928,7 +1120,16 @@ static void run_fold(const FoldArgs& one, const JobTable<FoldArgs>& tab, int gri
 
 template <int N, bool TABLE>
 static void run_inv_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int grid, int gx, int TS,
-                         const float2* tws, cudaStream_t s) {
+                         const float2* tws, cudaStream_t s, const float2* tw32) {
+    if constexpr (N == 4096) {
+        if (!tw32) fail(RIMO_ERR_STATE, "8192-point column transforms without their twiddle table");
+        const size_t sm = (size_t)(8192 + 8192 / 16) * sizeof(float2) + 8192 / 32 + 16;
+        if (grid == 0) return;
+        if (grid % 4 != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
+        set_smem(inv_cols32_kernel<TABLE>, sm);
+        launch_clustered(inv_cols32_kernel<TABLE>, grid, 256, sm, 4, s, one, tab, gx, tile_shift(TS), tw32);
+        return;
+    }
     constexpr int RB = rows_per_block<N>();
     constexpr int C = cluster_of<RB>();
     const int ntv = (2 * N) / TS;
@@ -975,7 +1176,7 @@ template <int N>
 static void fwd_cols(const rimo_plan* p, int bin, const float2* At, float2* X, cudaStream_t s) {
     const RowSel sel = fwd_sel(p, bin);
     run_fwd_cols<N, false>(cols_job(p, bin, At, X, sel), no_table<ColsJob>(),
-                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->TS, p->tab.tws_y, s);
+                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->TS, p->tab.tws_y, s, p->tab.tws32);
 }
 
 template <int N>
@@ -985,7 +1186,7 @@ static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStre
                     no_table<FoldArgs>(), br.n1 - br.n0, s);
     const RowSel sel = inv_sel(p, bin);
     run_inv_cols<N, false>(cols_job(p, bin, p->d_X, B, sel), no_table<ColsJob>(),
-                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->gx, p->TS, p->tab.tws_y, s);
+                           sel_blocks(p, bin, sel, rows_per_block<N>()), p->gx, p->TS, p->tab.tws_y, s, p->tab.tws32);
 }
 
 template <int N>
@@ -1001,6 +1202,7 @@ struct WideFft {
     int nx = 0, ny = 0, gx = 0, TS = 0, ngroups = 0;
     const float2* tws_x = nullptr;
     const float2* tws_y = nullptr;
+    const float2* tws32 = nullptr;
     struct Pass {
         void* jobs = nullptr;
         int* first = nullptr;
@@ -1046,6 +1248,7 @@ WideFft* wide_fft_create(const std::vector<WideJob>& jobs, const std::vector<con
         w->TS = p0->TS;
         w->tws_x = p0->tab.tws_x;
         w->tws_y = p0->tab.tws_y;
+        w->tws32 = p0->tab.tws32;
         w->ngroups = (int)x.size();
         const int rb = 4096 / p0->nx;  // rows per block of every pass (nx = ny)
         std::vector<RowsJob> rf, ri;
@@ -1101,7 +1304,7 @@ static void wide_fwd_n(const WideFft* w, cudaStream_t s) {
     std::memset(&r1, 0, sizeof(r1));
     std::memset(&c1, 0, sizeof(c1));
     run_fwd_rows<N, true>(r1, table_of<RowsJob>(w->rows_fwd), w->rows_fwd.blocks, w->ny, w->tws_x, s);
-    run_fwd_cols<N, true>(c1, table_of<ColsJob>(w->cols_fwd), w->cols_fwd.blocks, w->TS, w->tws_y, s);
+    run_fwd_cols<N, true>(c1, table_of<ColsJob>(w->cols_fwd), w->cols_fwd.blocks, w->TS, w->tws_y, s, w->tws32);
 }
 
 template <int N>
@@ -1113,7 +1316,8 @@ static void wide_inv_n(const WideFft* w, int real_only, cudaStream_t s) {
     std::memset(&c1, 0, sizeof(c1));
     std::memset(&f1, 0, sizeof(f1));
     run_fold<true>(f1, table_of<FoldArgs>(w->fold), w->fold.blocks, s);
-    run_inv_cols<N, true>(c1, table_of<ColsJob>(w->cols_inv), w->cols_inv.blocks, w->gx, w->TS, w->tws_y, s);
+    run_inv_cols<N, true>(c1, table_of<ColsJob>(w->cols_inv), w->cols_inv.blocks, w->gx, w->TS, w->tws_y, s,
+                          w->tws32);
     run_inv_rows<N, true>(r1, table_of<RowsJob>(w->rows_inv), w->group, w->rows_inv.blocks, w->ny, 0, real_only,
                           w->tws_x, s);
 }

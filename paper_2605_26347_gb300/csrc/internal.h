@@ -91,6 +91,8 @@ struct BinRange {
 struct DevTables {
     float2* tws_x = nullptr;   // Stockham stage twiddle tables for the 2 nx-point transforms
     float2* tws_y = nullptr;   // ... and the 2 ny-point transforms
+    float2* tws32 = nullptr;   // 8192-point transforms with 32 points per thread (radix 32, 16,
+                               // 16): W_512^{r j} at [r 32 + j], W_8192^{r j} at [512 + r 512 + j]
     float4* zq = nullptr;      // [|i_c|][|j_c|], (ny/2+1) x (nx/2+1): sqrt(1-l^2-m^2)-1 as a float pair, |Z_p|
     float* kb_coef = nullptr;  // Horner coefficients of KB(t) in rho = 1 - (2t/J)^2
     int kb_nterm = 0;

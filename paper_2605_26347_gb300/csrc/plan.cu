@@ -177,6 +177,20 @@ static void build_tables(rimo_plan* p, cudaStream_t s) {
     };
     p->tab.tws_x = upload(p, stage_twiddles(2 * nx), s);
     p->tab.tws_y = upload(p, stage_twiddles(2 * ny), s);
+    if (ny == 4096) {  // the 8192-point column passes run with 32 points per thread
+        std::vector<float2> t(512 + 8192);
+        for (int r = 0; r < 16; ++r) {
+            for (int j = 0; j < 32; ++j) {
+                const double a = -2.0 * M_PI * (double)r * j / 512.0;
+                t[(size_t)r * 32 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+            for (int j = 0; j < 512; ++j) {
+                const double a = -2.0 * M_PI * (double)r * j / 8192.0;
+                t[512 + (size_t)r * 512 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        }
+        p->tab.tws32 = upload(p, t, s);
+    }
     // Z_p on the quarter plane [|i_c|][|j_c|]: (n - 1) as a float pair for the w-phase and
     // |Z_p| = gc_x gc_y [/ n] (the grid correction is even in j_c and i_c), in FP64 then rounded
     const int qx = nx / 2 + 1, qy = ny / 2 + 1;
