@@ -751,10 +751,12 @@ struct FoldArgs {
     int ntu, ntv, TS, H, PW, gy;
 };
 
-template <bool TABLE>
+// TSC: the tile side (32 or 64) as a compile-time constant, so the cell indexing is shifts
+template <bool TABLE, int TSC>
 __global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ FoldArgs one, const JobTable<FoldArgs> tab) {
     int bk;
     const FoldArgs& F = block_job<TABLE>(one, tab, bk);
+    constexpr int TS = TSC;
     const int tile = F.tiles[bk];
     const int tu = tile / F.ntv, tv = tile - tu * F.ntv;
     const int tu1 = tu == 0 ? F.ntu - 1 : tu - 1, tv1 = tv == 0 ? F.ntv - 1 : tv - 1;
@@ -789,32 +791,50 @@ __global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ FoldA
     auto in = [](const Rng& r, int a, int b) {
         return (unsigned)(a - r.a) < (unsigned)r.na && (unsigned)(b - r.b) < (unsigned)r.nb;
     };
-    const Rng r00 = rng(x00, 0, 0), r10 = rng(x10, F.TS, 0), r01 = rng(x01, 0, F.TS), r11 = rng(x11, F.TS, F.TS);
+    const Rng r00 = rng(x00, 0, 0), r10 = rng(x10, TS, 0), r01 = rng(x01, 0, TS), r11 = rng(x11, TS, TS);
     const float2* __restrict__ patch = F.patch;
     float2* __restrict__ Xh = F.Xh;
     // every box covers all the cells its patch gives this tile (dense units): no per-cell test
     auto covers = [](const Rng& r, int na, int nb) { return r.a <= 0 && r.a + r.na >= na && r.b <= 0 && r.b + r.nb >= nb; };
-    if ((s00 < 0 || covers(r00, F.TS, F.TS)) && (s10 < 0 || covers(r10, F.H, F.TS)) &&
-        (s01 < 0 || covers(r01, F.TS, F.H)) && (s11 < 0 || covers(r11, F.H, F.H))) {
-        for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
-            const int a = e / F.TS, b = e - a * F.TS;
-            float2 acc = make_float2(0.f, 0.f);
-            if (s00 >= 0) acc = patch[s00 * np + a * F.PW + b];
-            if (a < F.H && s10 >= 0) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
-            if (b < F.H && s01 >= 0) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
-            if (a < F.H && b < F.H && s11 >= 0) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
-            Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
+    const bool dense = (s00 < 0 || covers(r00, TS, TS)) && (s10 < 0 || covers(r10, F.H, TS)) &&
+                       (s01 < 0 || covers(r01, TS, F.H)) && (s11 < 0 || covers(r11, F.H, F.H));
+    // one cell of the tile: the four sources (predicated), summed in a fixed order
+    auto cell = [&](int e, float2& v) {
+        const int a = e / TS, b = e - a * TS;
+        const bool k00 = dense ? s00 >= 0 : in(r00, a, b);
+        const bool k10 = dense ? (a < F.H && s10 >= 0) : in(r10, a, b);
+        const bool k01 = dense ? (b < F.H && s01 >= 0) : in(r01, a, b);
+        const bool k11 = dense ? (a < F.H && b < F.H && s11 >= 0) : in(r11, a, b);
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 p00 = k00 ? __ldg(&patch[s00 * np + a * F.PW + b]) : z;
+        const float2 p10 = k10 ? __ldg(&patch[s10 * np + (a + TS) * F.PW + b]) : z;
+        const float2 p01 = k01 ? __ldg(&patch[s01 * np + a * F.PW + b + TS]) : z;
+        const float2 p11 = k11 ? __ldg(&patch[s11 * np + (a + TS) * F.PW + b + TS]) : z;
+        v = k00 ? p00 : z;
+        if (k10) v = cadd(v, p10);
+        if (k01) v = cadd(v, p01);
+        if (k11) v = cadd(v, p11);
+    };
+    auto dst = [&](int e) {
+        const int a = e / TS, b = e - a * TS;
+        return Xh + (size_t)(tu * TS + a) * F.gy + tv * TS + b;
+    };
+    if constexpr (TS == 32) {
+        // the four cells of a thread: every load issued before the stores (per 4096^2/50M
+        // apply, inverse cols + fold 6.91 -> 6.72 ms against one cell at a time with a
+        // runtime tile side; the 16 cells of a 64-wide tile at once took 80 registers and
+        // slowed the wideband batch, 102.5 -> 114.2 ms, so 64-wide tiles go one at a time)
+        float2 acc[4];
+#pragma unroll
+        for (int it = 0; it < 4; ++it) cell(threadIdx.x + 256 * it, acc[it]);
+#pragma unroll
+        for (int it = 0; it < 4; ++it) *dst(threadIdx.x + 256 * it) = acc[it];
+    } else {
+        for (int e = threadIdx.x; e < TS * TS; e += 256) {
+            float2 v;
+            cell(e, v);
+            *dst(e) = v;
         }
-        return;
-    }
-    for (int e = threadIdx.x; e < F.TS * F.TS; e += blockDim.x) {
-        const int a = e / F.TS, b = e - a * F.TS;
-        float2 acc = make_float2(0.f, 0.f);
-        if (in(r00, a, b)) acc = patch[s00 * np + a * F.PW + b];
-        if (in(r10, a, b)) acc = cadd(acc, patch[s10 * np + (a + F.TS) * F.PW + b]);
-        if (in(r01, a, b)) acc = cadd(acc, patch[s01 * np + a * F.PW + b + F.TS]);
-        if (in(r11, a, b)) acc = cadd(acc, patch[s11 * np + (a + F.TS) * F.PW + b + F.TS]);
-        Xh[(size_t)(tu * F.TS + a) * F.gy + tv * F.TS + b] = acc;
     }
 }
 
@@ -1113,9 +1133,10 @@ static void run_fwd_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int g
 }
 
 template <bool TABLE>
-static void run_fold(const FoldArgs& one, const JobTable<FoldArgs>& tab, int grid, cudaStream_t s) {
+static void run_fold(const FoldArgs& one, const JobTable<FoldArgs>& tab, int grid, int TS, cudaStream_t s) {
     if (grid == 0) return;
-    fold_kernel<TABLE><<<grid, 256, 0, s>>>(one, tab);
+    if (TS == 32) fold_kernel<TABLE, 32><<<grid, 256, 0, s>>>(one, tab);
+    else fold_kernel<TABLE, 64><<<grid, 256, 0, s>>>(one, tab);  // plans hold TS = 32 or 64
 }
 
 template <int N, bool TABLE>
@@ -1183,7 +1204,7 @@ template <int N>
 static void inv_cols(const rimo_plan* p, int bin, bool holo, float2* B, cudaStream_t s) {
     const auto& br = p->bins[bin];
     run_fold<false>(fold_args(p, bin, holo ? p->d_hpatch : p->d_patch, holo ? p->d_hslot : nullptr, p->d_X),
-                    no_table<FoldArgs>(), br.n1 - br.n0, s);
+                    no_table<FoldArgs>(), br.n1 - br.n0, p->TS, s);
     const RowSel sel = inv_sel(p, bin);
     run_inv_cols<N, false>(cols_job(p, bin, p->d_X, B, sel), no_table<ColsJob>(),
                            sel_blocks(p, bin, sel, rows_per_block<N>()), p->gx, p->TS, p->tab.tws_y, s, p->tab.tws32);
@@ -1315,7 +1336,7 @@ static void wide_inv_n(const WideFft* w, int real_only, cudaStream_t s) {
     std::memset(&r1, 0, sizeof(r1));
     std::memset(&c1, 0, sizeof(c1));
     std::memset(&f1, 0, sizeof(f1));
-    run_fold<true>(f1, table_of<FoldArgs>(w->fold), w->fold.blocks, s);
+    run_fold<true>(f1, table_of<FoldArgs>(w->fold), w->fold.blocks, w->TS, s);
     run_inv_cols<N, true>(c1, table_of<ColsJob>(w->cols_inv), w->cols_inv.blocks, w->gx, w->TS, w->tws_y, s,
                           w->tws32);
     run_inv_rows<N, true>(r1, table_of<RowsJob>(w->rows_inv), w->group, w->rows_inv.blocks, w->ny, 0, real_only,
