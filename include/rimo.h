@@ -166,6 +166,10 @@ typedef struct rimo_plan_info {
     int64_t box_cells;         /* sum over the units of their box (the cells their   */
                                /* footprints reach; a split tile's slices: whole     */
                                /* patches): X cells staged and patch cells stored    */
+    int64_t n_needed;          /* needed uv-tiles summed over the bins (tiles of X   */
+                               /* the forward transform stores and the fold writes)  */
+    int64_t sel_rows;          /* grid rows the column passes transform, summed over */
+                               /* the bins (the rows of tile rows with a needed tile)*/
 } rimo_plan_info;
 
 typedef struct rimo_plan* rimo_plan_t;

@@ -75,6 +75,8 @@ class PlanInfo(C.Structure):
         ("h_nnz", C.c_int64),
         ("n_units", C.c_int64),
         ("box_cells", C.c_int64),
+        ("n_needed", C.c_int64),
+        ("sel_rows", C.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -626,6 +626,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         }
         p->d_need_list = upload(p, nl, s);
         p->need_host = nl;
+        p->info.n_needed = (int64_t)nl.size();
         // tile rows with a needed tile: the column passes transform only their grid rows
         p->trows.assign(P, {});
         for (int b = 0; b < P; ++b)
@@ -635,6 +636,8 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
                         p->trows[b].push_back((uint16_t)tu);
                         break;
                     }
+        p->info.sel_rows = 0;
+        for (int b = 0; b < P; ++b) p->info.sel_rows += (int64_t)p->trows[b].size() * TS;
     }
     p->d_patch = (float2*)dev_alloc(p, (size_t)std::max(1, p->max_tiles_bin) * p->PW * p->PW * sizeof(float2));
     p->d_counter = (int32_t*)dev_alloc(p, (size_t)P * sizeof(int32_t));
