@@ -7,10 +7,10 @@
 // taps of consecutive visibilities of a tile are one contiguous byte range.
 //
 // Kernel.  Persistent thread blocks (one per SM) take work units (a uv-tile, or a slice
-// of a heavy one) from a heaviest-first schedule: the next one through an atomic counter
-// when X patches are prefetched (a block that started late or drew light units takes more;
-// 26.31 -> 25.10 ms per 4096^2/50M apply against a fixed snake order), in snake order
-// otherwise.  For a unit, the block stages the box of grid cells its visibilities'
+// of a heavy one) from a heaviest-first schedule: for plans of dense units (8 chunks of
+// visibilities or more on average, X patches prefetched) the next one through an atomic
+// counter (a block that started late or drew light units takes more; 26.31 -> 25.10 ms per
+// 4096^2/50M apply against a fixed snake order), else in the snake order.  For a unit, the block stages the box of grid cells its visibilities'
 // footprints reach (within the (TS + H)^2 patch, H = largest tile side - 1) in shared
 // memory while a producer warp streams the taps of GTG_CHUNK visibilities at a time with
 // bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) through a
@@ -675,7 +675,8 @@ static void gtg_run(const rimo_plan* p, int bin, const float2* y_in, float2* y_o
     A.one = gtg_job(p, bin, p->d_X, p->d_patch);
     A.sched = p->d_sched + br.t0;
     A.nunits = nu;
-    A.counter = p->d_counter + bin;  // zeroed at the start of every apply
+    // dense units take the dynamic schedule (zeroed counter at the start of every apply)
+    A.counter = (double)(br.ve - br.vb) / nu >= 8.0 * GTG_CV ? p->d_counter + bin : nullptr;
     A.y_in = y_in;
     A.y_out = y_out;
     size_t sm = 0;
@@ -782,7 +783,7 @@ WideGtg* wide_gtg_create(const std::vector<WideJob>& jobs, cudaStream_t s) {
         w->A.jobs = w->jobs;
         w->A.queue = w->queue;
         w->A.nunits = (int)q.size();
-        w->A.counter = w->counter;
+        w->A.counter = (double)nvis / std::max<int64_t>(1, nun) >= 8.0 * GTG_CV ? w->counter : nullptr;
         if ((int64_t)w->A.nunits != w->units) fail(RIMO_ERR_UNSUPPORTED, "too many work units for one launch");
         w->grid = (int)std::min<int64_t>(w->units, p0->n_sm);
     } catch (...) {
