@@ -1122,14 +1122,14 @@ static void run_fwd_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int g
         if (grid == 0) return;
         set_smem(fwd_cols32_kernel<TABLE>, sm);
         fwd_cols32_kernel<TABLE><<<grid, 256, sm, s>>>(one, tab, tile_shift(TS), tw32);
-        return;
+    } else {
+        constexpr int RG = rows_per_block<N>();
+        const int ntv = (2 * N) / TS;
+        const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
+        if (grid == 0) return;
+        set_smem(fwd_cols_kernel<N, RG, TABLE>, sm);
+        fwd_cols_kernel<N, RG, TABLE><<<grid, RG * N / 8, sm, s>>>(one, tab, tile_shift(TS), tws);
     }
-    constexpr int RG = rows_per_block<N>();
-    const int ntv = (2 * N) / TS;
-    const size_t sm = (size_t)RG * (2 * N + N / 8) * sizeof(float2) + (size_t)RG * ntv + 16;
-    if (grid == 0) return;
-    set_smem(fwd_cols_kernel<N, RG, TABLE>, sm);
-    fwd_cols_kernel<N, RG, TABLE><<<grid, RG * N / 8, sm, s>>>(one, tab, tile_shift(TS), tws);
 }
 
 template <bool TABLE>
@@ -1149,22 +1149,22 @@ static void run_inv_cols(const ColsJob& one, const JobTable<ColsJob>& tab, int g
         if (grid % 4 != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
         set_smem(inv_cols32_kernel<TABLE>, sm);
         launch_clustered(inv_cols32_kernel<TABLE>, grid, 256, sm, 4, s, one, tab, gx, tile_shift(TS), tw32);
-        return;
-    }
-    constexpr int RB = rows_per_block<N>();
-    constexpr int C = cluster_of<RB>();
-    const int ntv = (2 * N) / TS;
-    const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2) + (size_t)RB * ntv + 16;
-    if (grid == 0) return;
-    // C consecutive blocks of a cluster stay in one tile row: TS / RB is a multiple of C
-    if constexpr (C > 1) {
-        if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
-        set_smem(inv_cols_kernel<N, RB, C, TABLE>, sm);
-        launch_clustered(inv_cols_kernel<N, RB, C, TABLE>, grid, RB * N / 8, sm, C, s, one, tab, gx, tile_shift(TS),
-                         tws);
     } else {
-        set_smem(inv_cols_kernel<N, RB, 1, TABLE>, sm);
-        inv_cols_kernel<N, RB, 1, TABLE><<<grid, RB * N / 8, sm, s>>>(one, tab, gx, tile_shift(TS), tws);
+        constexpr int RB = rows_per_block<N>();
+        constexpr int C = cluster_of<RB>();
+        const int ntv = (2 * N) / TS;
+        const size_t sm = (size_t)RB * (2 * N + N / 8) * sizeof(float2) + (size_t)RB * ntv + 16;
+        if (grid == 0) return;
+        // C consecutive blocks of a cluster stay in one tile row: TS / RB is a multiple of C
+        if constexpr (C > 1) {
+            if (grid % C != 0) fail(RIMO_ERR_UNSUPPORTED, "grid rows do not fill the transposed-store clusters");
+            set_smem(inv_cols_kernel<N, RB, C, TABLE>, sm);
+            launch_clustered(inv_cols_kernel<N, RB, C, TABLE>, grid, RB * N / 8, sm, C, s, one, tab, gx,
+                             tile_shift(TS), tws);
+        } else {
+            set_smem(inv_cols_kernel<N, RB, 1, TABLE>, sm);
+            inv_cols_kernel<N, RB, 1, TABLE><<<grid, RB * N / 8, sm, s>>>(one, tab, gx, tile_shift(TS), tws);
+        }
     }
 }
 

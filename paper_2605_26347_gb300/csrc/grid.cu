@@ -10,11 +10,12 @@
 // of a heavy one) from a heaviest-first schedule: for plans of dense units (8 chunks of
 // visibilities or more on average, X patches prefetched) the next one through an atomic
 // counter (a block that started late or drew light units takes more; 26.31 -> 25.10 ms per
-// 4096^2/50M apply against a fixed snake order), else in the snake order.  For a unit, the block stages the box of grid cells its visibilities'
-// footprints reach (within the (TS + H)^2 patch, H = largest tile side - 1) in shared
-// memory while a producer warp streams the taps of GTG_CHUNK visibilities at a time with
-// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) through a
-// shared-memory ring of up to GTG_NBUF chunks.
+// 4096^2/50M apply against a fixed snake order), else in the snake order.  For a unit,
+// the block stages the box of grid cells its visibilities' footprints reach (within the
+// (TS + H)^2 patch, H = largest tile side - 1) in shared memory while a producer warp
+// streams the taps of GTG_CHUNK visibilities at a time with bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier) through a shared-memory ring of up to
+// GTG_NBUF chunks.
 //   de-grid : one warp per visibility reads its S x S taps from shared memory (lanes = two
 //             rows of 16 columns), gathers the patch and reduces y_k with warp shuffles;
 //   grid    : the same warp adds conj(taps) y_k into the block's shared accumulator patch
