@@ -106,6 +106,18 @@ typedef enum rimo_n_weight {
  *                     2 = shuffled by a counter-based SplitMix64 hash of the visibility
  *                     index.  Results agree within rounding (the grid step sums exactly
  *                     in fixed point; only the split of heavy tiles into units moves).
+ *   shard_count,      level-2 distribution of Section 3.5 (G's Fourier blocks of every
+ *   shard_rank        w-bin over workers): with shard_count >= 2, shard_count plans made
+ *                     from the same uvw and parameters but shard_rank 0 .. shard_count - 1
+ *                     share the w-stack and the uv-tiles, and each keeps the tiles of every
+ *                     w-bin whose place in the bin's radial order (distance from the uv
+ *                     origin; ties by tile row, then column) is shard_rank modulo
+ *                     shard_count: it stores G and applies the operator for their
+ *                     visibilities only.  Phi writes those visibilities' y (the others are
+ *                     left as they are); the Phi^dagger and Phi^dagger Phi images of the
+ *                     shard plans sum to the whole operator's (Eq. 7: G_p^dagger G_p is a
+ *                     sum over visibilities).  Stored G only (mode STORED_G, or AUTO
+ *                     choosing it); 0 or 1: no sharding (the default).
  */
 typedef struct rimo_plan_params {
     int32_t nx, ny;
@@ -128,6 +140,8 @@ typedef struct rimo_plan_params {
     int64_t block_bytes_max;
     int32_t wkernel_table;
     int32_t uv_order;
+    int32_t shard_count;
+    int32_t shard_rank;
 } rimo_plan_params;
 
 /* Results of planning (stage 1 of Fig. 3) and the state of a plan. */
@@ -264,8 +278,9 @@ rimo_status rimo_plan_get_bins(rimo_plan_t plan, double* w_stack, int32_t* bins,
  * Plans without stored G (surrogate, on-the-fly, holographic before H is built) generate
  * the requested visibilities' bins into their tap scratch, as an apply does, and copy
  * from there; such a call must not overlap an apply of the same plan.
- * Errors: INVALID_ARG, STATE (surrogate plan without a surrogate), UNSUPPORTED
- * (holographic plan whose tiles were folded into H), CUDA.
+ * Errors: INVALID_ARG (also a visibility that a shard plan does not hold), STATE
+ * (surrogate plan without a surrogate), UNSUPPORTED (holographic plan whose tiles were
+ * folded into H), CUDA.
  */
 rimo_status rimo_plan_get_tiles(rimo_plan_t plan, const int64_t* idx, int64_t n, int32_t* g0,
                                 int32_t* h0, int32_t* S, rimo_cfloat* taps, void* stream);

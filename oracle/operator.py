@@ -210,20 +210,28 @@ class Operator:
             out += np.conj(self.z_layer(p)) * self.adj_grid(Xh)
         return out
 
-    def phi_adj_phi(self, x: np.ndarray, real_part_only: bool = False, bins=None) -> np.ndarray:
-        """sum_p Phi_p^dagger Phi_p x (Eq. 7), over all w-bins or the listed ones."""
+    def phi_adj_phi(self, x: np.ndarray, real_part_only: bool = False, bins=None, vis=None) -> np.ndarray:
+        """sum_p Phi_p^dagger Phi_p x (Eq. 7), over all w-bins or the listed ones; with `vis`
+        (boolean, one entry per visibility) only the selected visibilities' rows of each G_p
+        (G_p^dagger G_p of Eq. 8 is a sum over the bin's visibilities)."""
         pp = self.pp
         x = np.asarray(x, dtype=np.complex128)
         out = np.zeros((pp.ny, pp.nx), dtype=np.complex128)
         for p in (range(self.plan.P) if bins is None else bins):
-            if self.G[p].shape[0] == 0:
+            G = self.G[p]
+            if vis is not None:
+                G = G[np.flatnonzero(np.asarray(vis, dtype=bool)[self.plan.bins == p])]
+            if G.shape[0] == 0:
                 continue
             Zp = self.z_layer(p)
             X = self.fwd_grid(Zp * x).ravel()
-            yp = self.G[p] @ X
+            yp = G @ X
             if self.w is not None:
-                yp = self.w[self.plan.bins == p] ** 2 * yp
-            Xh = (self.G[p].conj().T @ yp).reshape(self.gx, self.gy)
+                wp = self.w[self.plan.bins == p]
+                if vis is not None:
+                    wp = wp[np.asarray(vis, dtype=bool)[self.plan.bins == p]]
+                yp = wp ** 2 * yp
+            Xh = (G.conj().T @ yp).reshape(self.gx, self.gy)
             out += np.conj(Zp) * self.adj_grid(Xh)
         return out.real.astype(np.complex128) if real_part_only else out
 

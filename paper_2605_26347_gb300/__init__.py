@@ -142,7 +142,9 @@ class Plan:
         torch = _torch()
         _check_image(x, self.ny, self.nx, "x")
         if y is None:
-            y = torch.empty(self.M, dtype=torch.complex64, device=x.device)
+            # a shard plan writes only its own visibilities: the others read as zero
+            y = (torch.zeros if self.params.shard_count >= 2 else torch.empty)(self.M, dtype=torch.complex64,
+                                                                             device=x.device)
         _lib.check(self._lib.rimo_apply_phi(self._h, x.data_ptr(), y.data_ptr(), _stream_ptr(stream)))
         return y
 

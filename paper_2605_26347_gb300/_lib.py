@@ -44,6 +44,8 @@ class PlanParams(C.Structure):
         ("block_bytes_max", C.c_int64),
         ("wkernel_table", C.c_int32),
         ("uv_order", C.c_int32),
+        ("shard_count", C.c_int32),
+        ("shard_rank", C.c_int32),
     ]
 
 

@@ -362,12 +362,13 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
         for (int64_t k0 = A.v0 + 2 * ((int64_t)blockIdx.x * BUILD_WARPS + warp); k0 < A.v0 + A.nvis;
              k0 += 2 * (int64_t)gridDim.x * BUILD_WARPS) {
             const int64_t k = k0 + hw;
-            const bool act = k < A.v0 + A.nvis;
             VisMeta mt{};
+            if (k < A.v0 + A.nvis) mt = A.meta[k];
+            // (visibilities of other shards have no taps)
+            const bool act = k < A.v0 + A.nvis && (mt.pos >> 24) != SHARD_SKIP;
             int Sw = 1, h = 0;
             float w = 0.f;
             if (act) {
-                mt = A.meta[k];
                 Sw = (int)((mt.pos >> 16) & 255) - 6;
                 h = Sw >> 1;
                 w = A.wr[k];
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) gbuild_kernel(BuildArgs A) {
          k += (int64_t)gridDim.x * BUILD_WARPS) {
         float tsum = 0.f;
         const VisMeta mt = A.meta[k];
+        if ((mt.pos >> 24) == SHARD_SKIP) continue;  // another shard's visibility: no taps (warp-uniform)
         const int S = (mt.pos >> 16) & 255;
         const int Sw = S - A.J + 1, h = Sw >> 1, hq = h + 1;
         const float w = A.wr[k];

@@ -53,6 +53,9 @@ struct VisMeta {
     uint32_t pos;
 };
 static_assert(sizeof(VisMeta) == 16, "VisMeta must stay 16 bytes");
+// Fourier-block number (pos >> 24) of a visibility that a shard plan does not hold: it has
+// no taps, and the G build passes it by
+constexpr uint32_t SHARD_SKIP = 255;
 
 // One uv-tile of one w-bin: the visibilities [vb, ve) of the sorted order whose first
 // cell falls in the TS x TS cells starting at (tu * TS, tv * TS).

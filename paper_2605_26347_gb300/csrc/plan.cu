@@ -94,6 +94,9 @@ void validate_params(const rimo_plan_params& q) {
     if (q.wkernel_table != 0 && (q.wkernel_table < 16 || q.wkernel_table > (1 << 22)))
         bad("wkernel_table must be 0 or in [16, 2^22]");
     if (q.uv_order < 0 || q.uv_order > 2) bad("uv_order must be 0, 1 or 2");
+    if (q.shard_count < 0 || q.shard_count > 1024) bad("shard_count must be in [0, 1024]");
+    if (q.shard_rank < 0 || q.shard_rank >= std::max(1, q.shard_count))
+        bad("shard_rank must be in [0, shard_count)");
     if (q.kb_beta < 0) bad("kb_beta must be >= 0");
 }
 
@@ -282,6 +285,9 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
     // (a holographic plan stores no G either: Phi and Phi^dagger, and Phi^dagger Phi until
     // rimo_build_holographic has run, generate exact tiles on the fly; Fig. 2 regimes b, c)
     const bool generated = surrogate || p->mode == RIMO_MODE_ONTHEFLY || p->mode == RIMO_MODE_HOLOGRAPHIC;
+    const bool sharded = q.shard_count >= 2;
+    if (sharded && p->mode != RIMO_MODE_STORED_G)
+        fail(RIMO_ERR_UNSUPPORTED, "a shard plan (shard_count >= 2) stores G: its mode must be STORED_G");
     if (surrogate && (q.kb_support + q.max_wsupport - 1 != 15))
         fail(RIMO_ERR_UNSUPPORTED, "the kernel surrogate generates 15 x 15 tiles: kb_support + max_wsupport - 1 must be 15");
 
@@ -415,11 +421,36 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         }
     }
     tstart.clear();
+    if (sharded) {
+        // level 2 (Section 3.5): this shard keeps the tiles of every bin whose place in the
+        // bin's radial order (ties by row, then column) is shard_rank modulo shard_count
+        total_bytes = 0.0;
+        for (int b = 0; b < P; ++b) {
+            std::vector<int> ix(tl[b].size());
+            std::iota(ix.begin(), ix.end(), 0);
+            std::sort(ix.begin(), ix.end(), [&](int x, int y) {
+                const T& A = tl[b][x];
+                const T& B = tl[b][y];
+                if (A.r != B.r) return A.r < B.r;
+                return A.tu != B.tu ? A.tu < B.tu : A.tv < B.tv;
+            });
+            std::vector<uint8_t> own(tl[b].size(), 0);
+            for (size_t i = 0; i < ix.size(); ++i) own[ix[i]] = (int)(i % (size_t)q.shard_count) == q.shard_rank;
+            std::vector<T> kept;
+            for (size_t i = 0; i < tl[b].size(); ++i)
+                if (own[i]) {
+                    kept.push_back(tl[b][i]);
+                    total_bytes += tl[b][i].bytes;
+                }
+            tl[b].swap(kept);
+        }
+    }
     double limit = q.block_bytes_max > 0 ? (double)q.block_bytes_max : 8.0 * 1073741824.0;
     if (q.n_blocks > 0) limit = std::ceil(total_bytes / q.n_blocks);
     limit = std::max(limit, std::ceil(total_bytes / 200.0));
     if (generated) limit = 1e300;  // one block per bin: its taps are generated into one scratch
-    std::vector<VisMeta> meta(M);
+    // visibilities of no tile of this plan (other shards') keep block SHARD_SKIP: no taps
+    std::vector<VisMeta> meta(M, VisMeta{0, 0u, (uint32_t)SHARD_SKIP << 24});
     std::vector<float> wr_s(M), pu_s(M), pv_s(M);
     p->bins.assign(P, BinRange());
     p->block_bytes.clear();
@@ -464,7 +495,7 @@ static void create_plan(const double* uvw, int64_t M, const rimo_plan_params& q,
         p->bins[b].w_hi = (float)p->w_stack[b];
         p->bins[b].w_lo = (float)(p->w_stack[b] - (double)p->bins[b].w_hi);
     }
-    if (p->block_bytes.size() > 255) fail(RIMO_ERR_INVALID_ARG, "more than 255 Fourier blocks");
+    if (p->block_bytes.size() > SHARD_SKIP) fail(RIMO_ERR_INVALID_ARG, "more than 255 Fourier blocks");
     // work units: active uv-tiles, split into units of at most `cap` visibilities so that
     // no unit outweighs a fraction of one SM's share of the bin; slots group the units of
     // a tile contiguously (merge groups), the schedule orders units heaviest first
@@ -807,6 +838,7 @@ rimo_status rimo_plan_get_tiles(rimo_plan_t p, const int64_t* idx, int64_t n, in
             RIMO_CUDA(cudaMemcpyAsync(&m, p->d_meta + i, sizeof(m), cudaMemcpyDeviceToHost, s));
             RIMO_CUDA(cudaStreamSynchronize(s));
             int du = m.pos & 255, dv = (m.pos >> 8) & 255, Sq = (m.pos >> 16) & 255, blk = m.pos >> 24;
+            if (blk == SHARD_SKIP) fail(RIMO_ERR_INVALID_ARG, "visibility held by another shard plan");
             // the tile containing sorted position i
             int b = p->bins_user[idx[q]];
             if (generated && b != have_bin) {  // tiles of generated plans: this bin, as an apply makes them
