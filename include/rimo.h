@@ -331,7 +331,8 @@ rimo_status rimo_apply_phi_adj_phi(rimo_plan_t plan, const rimo_cfloat* x_dev,
  * cell are many.  Built bin by bin through a temporary of the bin's dense rows.  Fails
  * with BUDGET (releasing what it built) when mem_budget_bytes is set and G plus H would
  * exceed it.  A second call does nothing.  info.h_bytes reports the rows and patches.
- * Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OOM, BUDGET, CUDA.
+ * Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED (surrogate plans; shard
+ * plans, shard_count >= 2), OOM, BUDGET, CUDA.
  */
 rimo_status rimo_build_holographic(rimo_plan_t plan, void* stream);
 

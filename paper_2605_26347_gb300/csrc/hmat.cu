@@ -759,6 +759,8 @@ rimo_status rimo_build_holographic(rimo_plan_t p, void* stream) {
     RIMO_API_BEGIN
     if (!p) fail(RIMO_ERR_INVALID_ARG, "null plan");
     if (p->mode == RIMO_MODE_SURROGATE) fail(RIMO_ERR_UNSUPPORTED, "H is built from exact tiles");
+    if (p->prm.shard_count >= 2)
+        fail(RIMO_ERR_UNSUPPORTED, "H of a shard plan: not provided (shard plans apply G^dagger G)");
     if (!p->h_built) build_holographic(p, (cudaStream_t)stream);
     RIMO_API_END
 }
